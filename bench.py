@@ -1,0 +1,345 @@
+"""Throughput benchmark: frames/s of the fused Gerchberg + Wiener reconstruction
+for 40x40 lenslets on a 128^2 grid (1000 seeded frames per step, k = 10).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl {gpu,reference}]
+
+One step = one pass of the whole path (embed, periodic fill, k Gerchberg
+iterations, final Wiener reconstruction) over a batch of 1000 frames that is
+already resident in HBM; one kernel launch per step. Between timed steps the
+L2 cache is flushed by writing a 256 MiB buffer (outside the timed region).
+The end-to-end figure (`e2e`) times the C-ABI host entry point, which copies
+the slopes in and the phase out inside the timed region.
+
+--impl reference times the FP64 CPU oracle (the plain implementation the GPU
+path is checked against) on the host cores, on a bounded sample of the same
+workload. Under torchrun only rank 0 runs it.
+
+With N > 1 (torchrun, one rank per GPU) each rank reconstructs its own batch
+(weak scaling, no collective on the data path); the reported time is the
+maximum over ranks.
+"""
+
+import argparse
+import hashlib
+import json
+import math
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# workload: 40x40 SPHERE-like lenslet array, D = 8 m, padded to 128^2
+N_LENSLETS = 40
+PAD = 3.2
+FRAMES = 1000
+ITERS = 10
+SIGMA = 0.1
+R0, L0 = 0.15, 25.0
+SEED0 = 1000
+METRIC = "frames/s at 40x40 lenslets (128² grid), ≤1e-5 rel err vs FP64; learned vs plain"
+
+# Roofline of the FFT-bound path: FP32 FMA peak from the unit counts and the
+# maximum SM clock (152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz).
+SMS, FP32_LANES, MAX_SM_MHZ = 152, 128, 2070.0
+
+
+def fp32_peak_tflops():
+    return SMS * FP32_LANES * 2 * MAX_SM_MHZ * 1e6 / 1e12
+
+
+def flops_per_frame(N, k):
+    """Algorithmic FFT flops: (2k + 1.5) complex N^2 transforms of 5 N^2 log2(N^2)
+    flops each (k forward + k inverse packed transforms in the loop, one forward
+    and half an inverse for the final real phase)."""
+    return (2 * k + 1.5) * 5.0 * N * N * math.log2(N * N)
+
+
+# DRAM bytes per launch of the fused kernel from an ncu capture, keyed by the
+# SHA-256 of the kernel source it was taken on (stale entries are ignored).
+TRAFFIC = {}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("fwr_gerchberg.cu", "fwr_internal.h"):
+        with open(os.path.join(ROOT, "paper_1705_04298_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+# ------------------------------------------------------------------ clocks --
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
+            self.path = os.path.join(ROOT, "gpurun_out", "clocks_gpu%d.csv" % self.gpu)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------- oracle -----
+
+def _oracle_worker(args):
+    slopes, mask, r0p, L0p = args
+    import oracle
+    t0 = time.perf_counter()
+    oracle.reconstruct(slopes, mask, PAD, ITERS, oracle.FILTER_WIENER, SIGMA ** 2, r0p, L0p)
+    return time.perf_counter() - t0
+
+
+class OraclePool:
+    """The FP64 oracle on all host cores: a spawn-started process pool, one
+    frame per process at a time, BLAS single-threaded in the workers."""
+
+    def __init__(self):
+        from paper_1705_04298_gb300 import synth
+        self.cores = os.cpu_count() or 1
+        for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ[var] = "1"
+        self.r0p, self.L0p = synth.pitch_units(N_LENSLETS, R0, L0)
+        self.sl, _, self.mask = synth.batch(N_LENSLETS, self.cores * 8, SEED0, SIGMA, R0, L0)
+        self.pool = mp.get_context("spawn").Pool(self.cores)
+        self.pool.map(_oracle_worker, [(self.sl[0], self.mask, self.r0p, self.L0p)] * self.cores)
+
+    def step(self, frames_per_core):
+        n = self.cores * frames_per_core
+        work = [(self.sl[i % len(self.sl)], self.mask, self.r0p, self.L0p) for i in range(n)]
+        t0 = time.perf_counter()
+        self.pool.map(_oracle_worker, work, chunksize=1)
+        return n, time.perf_counter() - t0
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def cpu_oracle_run(frames_per_core=6):
+    """Bounded sample (about 10 s of CPU work) of the workload on the oracle."""
+    pool = OraclePool()
+    try:
+        n, wall = pool.step(frames_per_core)
+    finally:
+        pool.close()
+    return {"value": n / wall, "unit": "frames/s", "cores": pool.cores, "kind": "oracle",
+            "sample": "%d frames (%d per core) of the 40x40 -> 128^2 k=%d Wiener workload, FP64 "
+                      "direct-DFT oracle, one process per core" % (n, frames_per_core, ITERS)}
+
+
+# ------------------------------------------------------------------ main ----
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    pool = OraclePool()
+    fpc = 2
+    try:
+        for _ in range(args.warmup):
+            pool.step(1)
+        walls, frames = [], 0
+        for _ in range(args.steps):
+            n, w = pool.step(fpc)
+            walls.append(w)
+            frames = n
+    finally:
+        pool.close()
+    ms_per_step = 1000.0 * statistics.median(walls)
+    value = frames / (ms_per_step / 1000.0)
+    cpu = {"value": value, "unit": "frames/s", "cores": pool.cores, "kind": "oracle",
+           "sample": "%d frames per step (%d per core) of the 40x40 -> 128^2 k=%d Wiener workload, "
+                     "FP64 direct-DFT oracle, one process per core" % (frames, fpc, ITERS)}
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "40x40 lenslets (D=8 m) padded to 128^2, seeded von Karman frames, "
+                                   "k=%d Gerchberg iterations, Wiener sigma=%g rad" % (ITERS, SIGMA),
+                       "frames_per_step": frames},
+            "cpu_baseline": cpu,
+            "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--iters", type=int, default=ITERS)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    rank, world, local = dist_env()
+    cpu_base = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # before the first GPU call: the oracle's process pool is spawned
+        cpu_base = cpu_oracle_run()
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.distributed.is_nccl_available() else "gloo")
+
+    from paper_1705_04298_gb300 import fwr, synth
+    k = args.iters
+    sl, _, mask = synth.batch(N_LENSLETS, FRAMES, SEED0 + rank * FRAMES, SIGMA, R0, L0)
+    r0p, L0p = synth.pitch_units(N_LENSLETS, R0, L0)
+    plan = fwr.Plan(mask, PAD, fwr.WIENER, SIGMA ** 2, r0p, L0p)
+    N = plan.N
+    slopes = torch.tensor(sl, dtype=torch.float32, device="cuda")
+    phase = torch.empty((FRAMES, N, N), dtype=torch.float32, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        plan.reconstruct(slopes, k, phase)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    times = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan.reconstruct(slopes, k, phase)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    barrier()
+    clk = clocks.stop()
+    gpu_launches = args.steps  # one fused kernel launch per step
+    total_ms = sum(times)
+    if dist is not None:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = t.item()
+    ms_per_step = total_ms / args.steps
+    value = FRAMES * world / (ms_per_step / 1000.0)
+
+    # end to end through the host entry point: H2D slopes, kernel, D2H phase
+    sh = torch.tensor(sl, dtype=torch.float32).pin_memory()
+    ph_host = torch.empty((FRAMES, N, N), dtype=torch.float32).pin_memory()
+    plan.reserve(FRAMES)
+    for _ in range(2):
+        plan.reconstruct_host(sh, k, ph_host)
+    torch.cuda.synchronize()
+    e2e_ms = []
+    for _ in range(max(3, args.steps // 2)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        plan.reconstruct_host(sh, k, ph_host)
+        torch.cuda.synchronize()
+        e2e_ms.append(1000.0 * (time.perf_counter() - t0))
+    e2e_step = statistics.median(e2e_ms)
+    if dist is not None:
+        t = torch.tensor([e2e_step], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_step = t.item()
+
+    if rank == 0:
+        fl = flops_per_frame(N, k) * FRAMES
+        achieved = fl / (ms_per_step / 1000.0) / 1e12
+        peak = fp32_peak_tflops()
+        src = kernel_source_hash()
+        line = {
+            "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "40x40 lenslets (D=8 m) padded to 128^2, %d seeded von Karman frames "
+                                   "per GPU, k=%d Gerchberg iterations, Wiener sigma=%g rad" % (FRAMES, k, SIGMA),
+                       "n_lenslets": N_LENSLETS, "grid": N, "frames_per_gpu": FRAMES, "iters": k,
+                       "filter": "wiener", "periodic": "before_each_fft", "l2": "flushed between steps",
+                       "valid_lenslets": plan.valid_count, "parallelism": "replicas (frames sharded)"},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": TRAFFIC.get(src),
+                         "kernel": "gerchberg_kernel<float,128>", "flops_per_launch": fl,
+                         "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 x 2.07 GHz (max SM clock)",
+                         "source_hash": src},
+            "e2e": {"value": FRAMES * world / (e2e_step / 1000.0), "unit": "frames/s",
+                    "h2d_bytes_per_step": int(sh.numel() * 4), "d2h_bytes_per_step": int(ph_host.numel() * 4)},
+            "gpu_launches": gpu_launches,
+            "clocks": clk,
+            "cpu_baseline": cpu_base,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

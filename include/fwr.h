@@ -1,0 +1,193 @@
+/*
+ * fwr.h - C ABI of the GB300 (sm_103a) iterative Fourier wave-front
+ * reconstructor: Gerchberg slope extension coupled to a Fourier-domain
+ * least-squares / Wiener reconstructor (Bond et al., "Iterative wave-front
+ * reconstruction in the Fourier domain", arXiv:1705.04298).
+ *
+ * The library computes, for every frame of Shack-Hartmann x/y slopes measured
+ * inside a pupil:
+ *   1. embed the n x n slopes in an N x N periodic grid at the centred offset
+ *      off = (N - n) / 2, zero outside the pupil             (Sec. 3.2)
+ *   2. optionally enforce the periodic condition: the last column of x slopes
+ *      takes minus the sum of its row, the last row of y slopes minus the sum
+ *      of its column                                          (Eq. PC)
+ *   3. FFT, least-squares phase estimate through the discrete measurement
+ *      model G, slopes re-synthesised through G, inverse FFT  (Algorithm 1,
+ *      steps 1-3; the LSQ formula of Sec. 3.3)
+ *   4. put the measured slopes back inside the pupil          (Algorithm 1,
+ *      step 4); repeat 2-4 `iters` times
+ *   5. final phase: FFT, Wiener or LSQ filter R, inverse FFT   (Eqs. 2-3)
+ *
+ * Conventions
+ *   - Grid index [m][c]: m is the row (y), c the column (x). Slopes are phase
+ *     differences across one lenslet, in radians; phase sample [m][c] is the
+ *     lower-left corner of slope cell [m][c]; lenslet (i, j) of the dense
+ *     input is grid cell (off + i, off + j).
+ *   - Measurement model (Eq. 4, lenslet sampling x averaging x gradient),
+ *     u = kx/N, v = ky/N in [-1/2, 1/2):
+ *       Gx = (e^{2 i pi u} - 1) sinc(v) e^{i pi v},
+ *       Gy = sinc(u) e^{i pi u} (e^{2 i pi v} - 1),
+ *     with the transverse factor 0 on the Nyquist row/column. 1/|G|^2 is 0 at
+ *     its nulls (piston and the waffle bin), so every output phase has zero
+ *     mean over the N x N grid.
+ *   - Wiener filter (Eq. 3, gamma = 1): R = G* / (|G|^2 + noise_var / W_phi)
+ *     with W_phi = 0.023 (r0/d)^(-5/3) (kappa^2 + (d/L0)^2)^(-11/6), kappa in
+ *     cycles per pitch. LSQ: R = G* / |G|^2. The filter inside the loop is
+ *     always LSQ (Sec. 3.3); `filter` selects the final one.
+ *   - All filter tables are built once per plan in FP64 on the host and
+ *     rounded to the kernel's precision.
+ *
+ * Memory and errors
+ *   - The caller owns every buffer it passes. `_dev` pointers are CUDA device
+ *     pointers on the plan's device; `_host` pointers are host memory (pinned
+ *     memory gives asynchronous copies).
+ *   - A plan owns its device tables. fwr_reconstruct* allocate nothing and
+ *     are asynchronous on `stream` (a cudaStream_t passed as void*; NULL is
+ *     the legacy default stream).
+ *   - Invalid arguments return FWR_ERR_ARG or FWR_ERR_UNSUPPORTED before any
+ *     launch. A failed launch returns FWR_ERR_CUDA. Conditions found on the
+ *     device (non-finite input slopes) set a sticky per-plan status word read
+ *     by fwr_get_status; the kernels never trap.
+ *   - A plan may be used from one host thread at a time.
+ */
+#ifndef FWR_H
+#define FWR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fwr_plan fwr_plan;
+
+typedef enum {
+    FWR_LSQ = 0,     /* R = G* / |G|^2 (gamma = 0 in Eq. 3) */
+    FWR_WIENER = 1   /* R = G* / (|G|^2 + noise_var / W_phi) (gamma = 1) */
+} fwr_filter;
+
+typedef enum {
+    FWR_OK = 0,
+    FWR_ERR_ARG = 1,          /* invalid argument; nothing launched */
+    FWR_ERR_UNSUPPORTED = 2,  /* valid but not supported by this build (grid size, precision) */
+    FWR_ERR_CUDA = 3,         /* CUDA runtime error (allocation, launch) */
+    FWR_ERR_NONFINITE = 4,    /* a measured slope was NaN or Inf (device status) */
+    FWR_ERR_TIMEOUT = 5       /* a bounded device wait gave up (device status) */
+} fwr_status;
+
+/* Option keys for fwr_plan_set_option. */
+#define FWR_OPT_PERIODIC 1
+/* Values of FWR_OPT_PERIODIC: where Eq. PC is applied. */
+#define FWR_PERIODIC_BEFORE_EACH_FFT 0 /* before every forward FFT, the final one included (default) */
+#define FWR_PERIODIC_FINAL_ONLY 1      /* once, before the final reconstruction (Algorithm 1 step 5) */
+#define FWR_PERIODIC_NONE 2            /* never */
+
+/*
+ * Create a plan for an n x n lenslet array (Sec. 2; Algorithm 1 input).
+ *   n_lenslets  n >= 2
+ *   pad_factor  N = next power of two >= ceil(pad_factor * n); N must be in
+ *               {16, 32, 64, 128, 256} and N >= n + 2 (the fill column/row
+ *               and the grid's last phase corners lie outside the pupil)
+ *   pupil_mask  HOST, n*n bytes row-major, nonzero = valid lenslet; copied
+ *               into the plan. At least one entry must be nonzero.
+ *   filter      final filter (fwr_filter)
+ *   noise_var   slope noise variance, rad^2 (>= 0; used by FWR_WIENER)
+ *   r0, L0      Fried parameter and outer scale IN LENSLET PITCHES (> 0 for
+ *               FWR_WIENER; ignored for FWR_LSQ)
+ * Allocates the plan's device tables on the current CUDA device.
+ * Returns FWR_OK and *out, or an error with *out = NULL.
+ */
+fwr_status fwr_plan_create(fwr_plan** out, int n_lenslets, double pad_factor,
+                           const uint8_t* pupil_mask, int filter, double noise_var,
+                           double r0, double L0);
+
+/* Free a plan and its device tables (NULL is ignored). Not stream-ordered:
+ * the caller makes sure no work using the plan is still running. */
+void fwr_plan_destroy(fwr_plan* plan);
+
+/* Padded grid size N of the plan, or -1 for NULL. */
+int fwr_plan_grid(const fwr_plan* plan);
+
+/* Number of valid lenslets in the plan's mask, or -1 for NULL. */
+int fwr_plan_valid_count(const fwr_plan* plan);
+
+/* Set a plan option (FWR_OPT_*). FWR_ERR_ARG for an unknown key or value. */
+fwr_status fwr_plan_set_option(fwr_plan* plan, int key, double value);
+
+/*
+ * Reconstruct n_frames frames in FP32 (Algorithm 1 + Eqs. 2-3).
+ *   slopes_dev  [n_frames][2][n][n] float, x slopes then y slopes; entries
+ *               outside the mask are ignored
+ *   iters       Gerchberg iterations, 0 <= iters <= 64 (0 = zero padding,
+ *               plus the periodic fill where the option asks for it)
+ *   phase_dev   [n_frames][N][N] float output, radians, zero mean
+ * n_frames = 0 is a no-op. All work is one persistent kernel launch.
+ */
+fwr_status fwr_reconstruct(fwr_plan* plan, const float* slopes_dev, int n_frames, int iters,
+                           float* phase_dev, void* stream);
+
+/*
+ * As fwr_reconstruct, with two optional extras.
+ *   ext_init_dev  [n_frames][2][N][N] initial slopes used OUTSIDE the pupil
+ *                 before the first iteration (a warm start), or NULL for 0
+ *   phase_dev     may be NULL (no final reconstruction)
+ *   ext_out_dev   [n_frames][2][N][N] output: the extended slopes that enter
+ *                 the final reconstruction (after the periodic fill where it
+ *                 applies), or NULL
+ */
+fwr_status fwr_reconstruct_ex(fwr_plan* plan, const float* slopes_dev, const float* ext_init_dev,
+                              int n_frames, int iters, float* phase_dev, float* ext_out_dev,
+                              void* stream);
+
+/*
+ * The same computation in FP64 throughout (tables, FFTs, filters). Same
+ * layouts with double elements. Supported for N <= 64 (an FP64 grid of
+ * 128^2 does not fit in one SM's shared memory): FWR_ERR_UNSUPPORTED
+ * otherwise. Meant for parity checks, not throughput.
+ */
+fwr_status fwr_reconstruct_f64(fwr_plan* plan, const double* slopes_dev, const double* ext_init_dev,
+                               int n_frames, int iters, double* phase_dev, double* ext_out_dev,
+                               void* stream);
+
+/*
+ * End-to-end FP32 call on HOST buffers: copies slopes_host
+ * ([n_frames][2][n][n]) to plan-owned device staging, reconstructs and copies
+ * the phase back to phase_host ([n_frames][N][N]), all on `stream`. The
+ * staging grows on demand (cudaMalloc on the first call with a larger
+ * n_frames; fwr_plan_reserve does it ahead). Returns after enqueueing; the
+ * caller synchronises `stream` before reading phase_host.
+ */
+fwr_status fwr_reconstruct_host(fwr_plan* plan, const float* slopes_host, int n_frames, int iters,
+                                float* phase_host, void* stream);
+
+/* Pre-allocate host-path staging for n_frames frames. */
+fwr_status fwr_plan_reserve(fwr_plan* plan, int n_frames);
+
+/*
+ * Batched 2-D FFT of n_frames complex N x N grids with the kernels' own
+ * shared-memory FFT (the transform used inside the loop), FP32 interleaved
+ * complex (re, im). Forward: X[ky][kx] = sum x[m][c] e^{-2 i pi (ky m + kx c)/N};
+ * inverse (inverse != 0) uses +i and no 1/N^2 scaling. N in {16,...,128};
+ * in_dev and out_dev may be the same buffer.
+ */
+fwr_status fwr_fft2(int N, const float* in_dev, float* out_dev, int n_frames, int inverse,
+                    void* stream);
+
+/*
+ * Read and clear the plan's sticky device status word. Synchronises the
+ * plan's device. FWR_OK, FWR_ERR_NONFINITE or FWR_ERR_TIMEOUT.
+ */
+fwr_status fwr_get_status(fwr_plan* plan);
+
+/* Static, human-readable name of a status code. */
+const char* fwr_status_string(fwr_status status);
+
+/* Text of the last CUDA error seen by the library on this thread ("" if none). */
+const char* fwr_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FWR_H */

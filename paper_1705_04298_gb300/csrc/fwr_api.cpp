@@ -1,0 +1,423 @@
+// C ABI of the reconstructor (declared in include/fwr.h): argument checks, the
+// FP64 filter builder and plan-owned device tables. Every step of the
+// reconstruction itself runs in the kernels of fwr_gerchberg.cu.
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "../../include/fwr.h"
+#include "fwr_internal.h"
+
+namespace {
+
+thread_local char g_last_error[256] = "";
+
+fwr_status cuda_fail(cudaError_t e, const char* where) {
+    std::snprintf(g_last_error, sizeof(g_last_error), "%s: %s", where, cudaGetErrorString(e));
+    return FWR_ERR_CUDA;
+}
+
+const double kPi = 3.14159265358979323846;
+const double kNullThreshold = 1e-14;
+
+// Device copies of one precision's tables.
+template <typename T> struct DevTables {
+    typedef typename fwr::cvec<T>::type V;
+    V* tw = nullptr;
+    V* A = nullptr;
+    V* Tt = nullptr;
+    T* iota = nullptr;
+    T* wfin = nullptr;
+};
+
+template <typename T> void free_tables(DevTables<T>& t) {
+    cudaFree(t.tw);
+    cudaFree(t.A);
+    cudaFree(t.Tt);
+    cudaFree(t.iota);
+    cudaFree(t.wfin);
+    t = DevTables<T>();
+}
+
+}  // namespace
+
+struct fwr_plan {
+    int n = 0, N = 0, off = 0, filter = 0, periodic = FWR_PERIODIC_BEFORE_EACH_FFT, nvalid = 0;
+    int device = 0;
+    double noise_var = 0, r0 = 0, L0 = 0;
+    uint8_t* d_mask = nullptr;
+    unsigned* d_status = nullptr;
+    DevTables<float> f32;
+    DevTables<double> f64;
+    // host-path staging
+    float* d_stage_in = nullptr;
+    float* d_stage_out = nullptr;
+    int stage_frames = 0;
+};
+
+namespace {
+
+int next_pow2(int x) {
+    int p = 1;
+    while (p < x) p *= 2;
+    return p;
+}
+
+double signed_freq(int k, int N) { return (k < N / 2 ? double(k) : double(k - N)) / N; }
+
+double sinc(double x) { return x == 0.0 ? 1.0 : std::sin(kPi * x) / (kPi * x); }
+
+// FP64 filter tables (Eq. 4 model, the LSQ weight of Sec. 3.3, the Wiener
+// weight of Eq. 3). Returned in the device layout of fwr::Tables.
+struct HostTables {
+    std::vector<double> tw, A, Tt;  // interleaved re, im; N entries each
+    std::vector<double> iota, wfin; // (N/2+1) * N
+};
+
+HostTables build_tables(int N, int filter, double noise_var, double r0, double L0) {
+    HostTables h;
+    h.tw.resize(2 * N);
+    h.A.resize(2 * N);
+    h.Tt.resize(2 * N);
+    for (int j = 0; j < N; ++j) {
+        const double ang = 2.0 * kPi * double(j) / double(N);
+        h.tw[2 * j] = std::cos(ang);
+        h.tw[2 * j + 1] = -std::sin(ang);
+        const double u = signed_freq(j, N);
+        // a(u) = e^{2 i pi u} - 1; exact at u = 0 and u = -1/2
+        double ar = std::cos(2.0 * kPi * u) - 1.0, ai = std::sin(2.0 * kPi * u);
+        if (j == 0) ar = ai = 0.0;
+        if (j == N / 2) { ar = -2.0; ai = 0.0; }
+        h.A[2 * j] = ar;
+        h.A[2 * j + 1] = ai;
+        // T(u) = sinc(u) e^{i pi u}; the Nyquist bin takes the mean of its two
+        // aliases, which is 0
+        const double s = sinc(u);
+        h.Tt[2 * j] = (j == N / 2) ? 0.0 : s * std::cos(kPi * u);
+        h.Tt[2 * j + 1] = (j == N / 2) ? 0.0 : s * std::sin(kPi * u);
+    }
+    const int H = N / 2;
+    h.iota.assign(size_t(H + 1) * N, 0.0);
+    h.wfin.assign(size_t(H + 1) * N, 0.0);
+    const double inv_n2 = 1.0 / (double(N) * double(N));  // inverse-DFT scale folded in
+    const double rho = r0, ell = L0;
+    for (int ky = 0; ky <= H; ++ky) {
+        for (int kx = 0; kx < N; ++kx) {
+            const double a2x = h.A[2 * kx] * h.A[2 * kx] + h.A[2 * kx + 1] * h.A[2 * kx + 1];
+            const double a2y = h.A[2 * ky] * h.A[2 * ky] + h.A[2 * ky + 1] * h.A[2 * ky + 1];
+            const double t2x = h.Tt[2 * kx] * h.Tt[2 * kx] + h.Tt[2 * kx + 1] * h.Tt[2 * kx + 1];
+            const double t2y = h.Tt[2 * ky] * h.Tt[2 * ky] + h.Tt[2 * ky + 1] * h.Tt[2 * ky + 1];
+            // |Gx|^2 = |a(u)|^2 |T(v)|^2, |Gy|^2 = |T(u)|^2 |a(v)|^2
+            const double g2 = a2x * t2y + t2x * a2y;
+            const size_t idx = size_t(ky) * N + kx;
+            if (g2 < kNullThreshold) continue;
+            h.iota[idx] = inv_n2 / g2;
+            if (filter == FWR_WIENER) {
+                const double u = signed_freq(kx, N), v = signed_freq(ky, N);
+                const double kappa2 = u * u + v * v;
+                const double wphi = 0.023 * std::pow(rho, -5.0 / 3.0) *
+                                    std::pow(kappa2 + 1.0 / (ell * ell), -11.0 / 6.0);
+                h.wfin[idx] = inv_n2 / (g2 + noise_var / wphi);
+            } else {
+                h.wfin[idx] = h.iota[idx];
+            }
+        }
+    }
+    return h;
+}
+
+template <typename T>
+fwr_status upload_tables(const HostTables& h, int N, DevTables<T>& d) {
+    typedef typename fwr::cvec<T>::type V;
+    const int H = N / 2;
+    std::vector<T> tw(2 * N), A(2 * N), Tt(2 * N), iota(size_t(H + 1) * N), wfin(size_t(H + 1) * N);
+    for (int i = 0; i < 2 * N; ++i) {
+        tw[i] = T(h.tw[i]);
+        A[i] = T(h.A[i]);
+        Tt[i] = T(h.Tt[i]);
+    }
+    for (size_t i = 0; i < iota.size(); ++i) {
+        iota[i] = T(h.iota[i]);
+        wfin[i] = T(h.wfin[i]);
+    }
+    cudaError_t e;
+    if ((e = cudaMalloc(&d.tw, N * sizeof(V))) != cudaSuccess) return cuda_fail(e, "cudaMalloc tables");
+    if ((e = cudaMalloc(&d.A, N * sizeof(V))) != cudaSuccess) return cuda_fail(e, "cudaMalloc tables");
+    if ((e = cudaMalloc(&d.Tt, N * sizeof(V))) != cudaSuccess) return cuda_fail(e, "cudaMalloc tables");
+    if ((e = cudaMalloc(&d.iota, iota.size() * sizeof(T))) != cudaSuccess) return cuda_fail(e, "cudaMalloc tables");
+    if ((e = cudaMalloc(&d.wfin, wfin.size() * sizeof(T))) != cudaSuccess) return cuda_fail(e, "cudaMalloc tables");
+    if ((e = cudaMemcpy(d.tw, tw.data(), N * sizeof(V), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(d.A, A.data(), N * sizeof(V), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(d.Tt, Tt.data(), N * sizeof(V), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(d.iota, iota.data(), iota.size() * sizeof(T), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(d.wfin, wfin.data(), wfin.size() * sizeof(T), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return cuda_fail(e, "cudaMemcpy tables");
+    return FWR_OK;
+}
+
+template <typename T>
+fwr::Tables<T> view(const DevTables<T>& d) {
+    fwr::Tables<T> t;
+    t.tw = d.tw;
+    t.A = d.A;
+    t.Tt = d.Tt;
+    t.iota = d.iota;
+    t.wfin = d.wfin;
+    return t;
+}
+
+bool supported_grid(int N) { return N == 16 || N == 32 || N == 64 || N == 128; }
+
+}  // namespace
+
+extern "C" {
+
+fwr_status fwr_plan_create(fwr_plan** out, int n, double pad_factor, const uint8_t* pupil_mask, int filter,
+                           double noise_var, double r0, double L0) {
+    if (!out) return FWR_ERR_ARG;
+    *out = nullptr;
+    if (n < 2 || !pupil_mask || !(pad_factor >= 1.0) || !std::isfinite(pad_factor)) return FWR_ERR_ARG;
+    if (filter != FWR_LSQ && filter != FWR_WIENER) return FWR_ERR_ARG;
+    if (!(noise_var >= 0.0) || !std::isfinite(noise_var)) return FWR_ERR_ARG;
+    if (filter == FWR_WIENER && (!(r0 > 0.0) || !(L0 > 0.0) || !std::isfinite(r0) || !std::isfinite(L0)))
+        return FWR_ERR_ARG;
+    const double want = std::ceil(pad_factor * n - 1e-9);
+    if (want > 4096.0) return FWR_ERR_UNSUPPORTED;
+    const int N = next_pow2(int(want));
+    if (N < n + 2) return FWR_ERR_ARG;
+    if (!supported_grid(N)) return FWR_ERR_UNSUPPORTED;
+    int nvalid = 0;
+    for (int i = 0; i < n * n; ++i) nvalid += pupil_mask[i] ? 1 : 0;
+    if (nvalid == 0) return FWR_ERR_ARG;
+
+    fwr_plan* p = new (std::nothrow) fwr_plan();
+    if (!p) return FWR_ERR_CUDA;
+    p->n = n;
+    p->N = N;
+    p->off = (N - n) / 2;
+    p->filter = filter;
+    p->noise_var = noise_var;
+    p->r0 = r0;
+    p->L0 = L0;
+    p->nvalid = nvalid;
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e != cudaSuccess) {
+        delete p;
+        return cuda_fail(e, "cudaGetDevice");
+    }
+    std::vector<uint8_t> m(size_t(n) * n);
+    for (int i = 0; i < n * n; ++i) m[i] = pupil_mask[i] ? 1 : 0;
+    fwr_status st = FWR_OK;
+    if ((e = cudaMalloc(&p->d_mask, m.size())) != cudaSuccess ||
+        (e = cudaMemcpy(p->d_mask, m.data(), m.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMalloc(&p->d_status, sizeof(unsigned))) != cudaSuccess ||
+        (e = cudaMemset(p->d_status, 0, sizeof(unsigned))) != cudaSuccess) {
+        st = cuda_fail(e, "plan allocation");
+    }
+    if (st == FWR_OK) {
+        HostTables h = build_tables(N, filter, noise_var, r0, L0);
+        st = upload_tables<float>(h, N, p->f32);
+        if (st == FWR_OK && N <= 64) st = upload_tables<double>(h, N, p->f64);
+    }
+    if (st != FWR_OK) {
+        fwr_plan_destroy(p);
+        return st;
+    }
+    *out = p;
+    return FWR_OK;
+}
+
+void fwr_plan_destroy(fwr_plan* p) {
+    if (!p) return;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(p->device);
+    free_tables(p->f32);
+    free_tables(p->f64);
+    cudaFree(p->d_mask);
+    cudaFree(p->d_status);
+    cudaFree(p->d_stage_in);
+    cudaFree(p->d_stage_out);
+    cudaSetDevice(prev);
+    delete p;
+}
+
+int fwr_plan_grid(const fwr_plan* p) { return p ? p->N : -1; }
+
+int fwr_plan_valid_count(const fwr_plan* p) { return p ? p->nvalid : -1; }
+
+fwr_status fwr_plan_set_option(fwr_plan* p, int key, double value) {
+    if (!p) return FWR_ERR_ARG;
+    if (key == FWR_OPT_PERIODIC) {
+        const int v = int(value);
+        if (double(v) != value || v < FWR_PERIODIC_BEFORE_EACH_FFT || v > FWR_PERIODIC_NONE) return FWR_ERR_ARG;
+        p->periodic = v;
+        return FWR_OK;
+    }
+    return FWR_ERR_ARG;
+}
+
+static fwr_status check_call(const fwr_plan* p, const void* slopes, int n_frames, int iters, const void* phase,
+                             const void* ext_out) {
+    if (!p || n_frames < 0 || iters < 0 || iters > 64) return FWR_ERR_ARG;
+    if (n_frames > 0 && !slopes) return FWR_ERR_ARG;
+    if (n_frames > 0 && !phase && !ext_out) return FWR_ERR_ARG;
+    return FWR_OK;
+}
+
+fwr_status fwr_reconstruct_ex(fwr_plan* p, const float* slopes, const float* ext_init, int n_frames, int iters,
+                              float* phase, float* ext_out, void* stream) {
+    fwr_status st = check_call(p, slopes, n_frames, iters, phase, ext_out);
+    if (st != FWR_OK) return st;
+    if (n_frames == 0) return FWR_OK;
+    fwr::Params<float> k;
+    k.tab = view(p->f32);
+    k.mask = p->d_mask;
+    k.slopes = slopes;
+    k.ext_init = ext_init;
+    k.phase = phase;
+    k.ext_out = ext_out;
+    k.n = p->n;
+    k.off = p->off;
+    k.F = n_frames;
+    k.iters = iters;
+    k.periodic = p->periodic;
+    k.status = p->d_status;
+    cudaError_t e = fwr::launch_gerchberg_f32(p->N, k, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? FWR_OK : cuda_fail(e, "gerchberg launch");
+}
+
+fwr_status fwr_reconstruct(fwr_plan* p, const float* slopes, int n_frames, int iters, float* phase, void* stream) {
+    if (!phase && n_frames > 0) return FWR_ERR_ARG;
+    return fwr_reconstruct_ex(p, slopes, nullptr, n_frames, iters, phase, nullptr, stream);
+}
+
+fwr_status fwr_reconstruct_f64(fwr_plan* p, const double* slopes, const double* ext_init, int n_frames, int iters,
+                               double* phase, double* ext_out, void* stream) {
+    fwr_status st = check_call(p, slopes, n_frames, iters, phase, ext_out);
+    if (st != FWR_OK) return st;
+    if (p->N > 64) return FWR_ERR_UNSUPPORTED;
+    if (n_frames == 0) return FWR_OK;
+    fwr::Params<double> k;
+    k.tab = view(p->f64);
+    k.mask = p->d_mask;
+    k.slopes = slopes;
+    k.ext_init = ext_init;
+    k.phase = phase;
+    k.ext_out = ext_out;
+    k.n = p->n;
+    k.off = p->off;
+    k.F = n_frames;
+    k.iters = iters;
+    k.periodic = p->periodic;
+    k.status = p->d_status;
+    cudaError_t e = fwr::launch_gerchberg_f64(p->N, k, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? FWR_OK : cuda_fail(e, "gerchberg f64 launch");
+}
+
+fwr_status fwr_plan_reserve(fwr_plan* p, int n_frames) {
+    if (!p || n_frames < 0) return FWR_ERR_ARG;
+    if (n_frames <= p->stage_frames) return FWR_OK;
+    cudaFree(p->d_stage_in);
+    cudaFree(p->d_stage_out);
+    p->d_stage_in = p->d_stage_out = nullptr;
+    p->stage_frames = 0;
+    const size_t in_b = size_t(n_frames) * 2 * p->n * p->n * sizeof(float);
+    const size_t out_b = size_t(n_frames) * p->N * p->N * sizeof(float);
+    cudaError_t e;
+    if ((e = cudaMalloc(&p->d_stage_in, in_b)) != cudaSuccess) return cuda_fail(e, "cudaMalloc staging");
+    if ((e = cudaMalloc(&p->d_stage_out, out_b)) != cudaSuccess) return cuda_fail(e, "cudaMalloc staging");
+    p->stage_frames = n_frames;
+    return FWR_OK;
+}
+
+fwr_status fwr_reconstruct_host(fwr_plan* p, const float* slopes_host, int n_frames, int iters, float* phase_host,
+                                void* stream) {
+    fwr_status st = check_call(p, slopes_host, n_frames, iters, phase_host, nullptr);
+    if (st != FWR_OK) return st;
+    if (!phase_host && n_frames > 0) return FWR_ERR_ARG;
+    if (n_frames == 0) return FWR_OK;
+    if ((st = fwr_plan_reserve(p, n_frames)) != FWR_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t in_b = size_t(n_frames) * 2 * p->n * p->n * sizeof(float);
+    const size_t out_b = size_t(n_frames) * p->N * p->N * sizeof(float);
+    cudaError_t e = cudaMemcpyAsync(p->d_stage_in, slopes_host, in_b, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(e, "H2D slopes");
+    st = fwr_reconstruct_ex(p, p->d_stage_in, nullptr, n_frames, iters, p->d_stage_out, nullptr, stream);
+    if (st != FWR_OK) return st;
+    e = cudaMemcpyAsync(phase_host, p->d_stage_out, out_b, cudaMemcpyDeviceToHost, s);
+    return e == cudaSuccess ? FWR_OK : cuda_fail(e, "D2H phase");
+}
+
+fwr_status fwr_fft2(int N, const float* in, float* out, int n_frames, int inverse, void* stream) {
+    if (!(N == 16 || N == 32 || N == 64 || N == 128) || n_frames < 0) return FWR_ERR_ARG;
+    if (n_frames == 0) return FWR_OK;
+    if (!in || !out) return FWR_ERR_ARG;
+    // one twiddle table per (device, N), built in FP64 and kept for the
+    // process lifetime
+    static std::mutex mu;
+    static std::map<std::pair<int, int>, float2*> cache;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    float2* tw = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        auto it = cache.find({dev, N});
+        if (it == cache.end()) {
+            std::vector<float2> h(N);
+            for (int j = 0; j < N; ++j) {
+                const double ang = 2.0 * kPi * double(j) / double(N);
+                h[j] = make_float2(float(std::cos(ang)), float(-std::sin(ang)));
+            }
+            if ((e = cudaMalloc(&tw, N * sizeof(float2))) != cudaSuccess) return cuda_fail(e, "cudaMalloc twiddles");
+            if ((e = cudaMemcpy(tw, h.data(), N * sizeof(float2), cudaMemcpyHostToDevice)) != cudaSuccess)
+                return cuda_fail(e, "cudaMemcpy twiddles");
+            cache[{dev, N}] = tw;
+        } else {
+            tw = it->second;
+        }
+    }
+    e = fwr::launch_fft2_f32(N, reinterpret_cast<const float2*>(in), reinterpret_cast<float2*>(out), n_frames,
+                             inverse, tw, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? FWR_OK : cuda_fail(e, "fft2 launch");
+}
+
+fwr_status fwr_get_status(fwr_plan* p) {
+    if (!p) return FWR_ERR_ARG;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(p->device);
+    unsigned v = 0;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(&v, p->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, sizeof(unsigned));
+    cudaSetDevice(prev);
+    if (e != cudaSuccess) return cuda_fail(e, "status read");
+    if (v & fwr::STATUS_NONFINITE) return FWR_ERR_NONFINITE;
+    if (v & fwr::STATUS_TIMEOUT) return FWR_ERR_TIMEOUT;
+    return FWR_OK;
+}
+
+const char* fwr_status_string(fwr_status s) {
+    switch (s) {
+        case FWR_OK: return "FWR_OK";
+        case FWR_ERR_ARG: return "FWR_ERR_ARG";
+        case FWR_ERR_UNSUPPORTED: return "FWR_ERR_UNSUPPORTED";
+        case FWR_ERR_CUDA: return "FWR_ERR_CUDA";
+        case FWR_ERR_NONFINITE: return "FWR_ERR_NONFINITE";
+        case FWR_ERR_TIMEOUT: return "FWR_ERR_TIMEOUT";
+        default: return "FWR_UNKNOWN_STATUS";
+    }
+}
+
+const char* fwr_last_error(void) { return g_last_error; }
+
+}  // extern "C"

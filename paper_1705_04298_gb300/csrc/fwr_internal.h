@@ -1,0 +1,53 @@
+// Internal interface between the C ABI (fwr_api.cpp) and the kernels
+// (fwr_gerchberg.cu). Not installed; the public interface is include/fwr.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fwr {
+
+template <typename T> struct cvec;
+template <> struct cvec<float> { typedef float2 type; };
+template <> struct cvec<double> { typedef double2 type; };
+
+// Per-plan filter tables, built in FP64 on the host (Eqs. 3-4, Sec. 3.3) and
+// rounded to T. Spectral tables cover rows ky = 0 .. N/2 only: both weights
+// are even in k, and the kernels visit each (k, -k) pair once from that half.
+template <typename T> struct Tables {
+    const typename cvec<T>::type* tw;  // [N]   e^{-2 i pi j / N}
+    const typename cvec<T>::type* A;   // [N]   a(u) = e^{2 i pi u} - 1
+    const typename cvec<T>::type* Tt;  // [N]   T(u) = sinc(u) e^{i pi u}, 0 at u = -1/2
+    const T* iota;                     // [(N/2+1) N] 1/|G|^2 / N^2 (0 at nulls)
+    const T* wfin;                     // [(N/2+1) N] final weight / N^2 (LSQ or Wiener)
+};
+
+template <typename T> struct Params {
+    Tables<T> tab;
+    const uint8_t* mask;  // [n n] device copy of the pupil mask
+    const T* slopes;      // [F][2][n][n]
+    const T* ext_init;    // [F][2][N][N] or nullptr
+    T* phase;             // [F][N][N] or nullptr
+    T* ext_out;           // [F][2][N][N] or nullptr
+    int n, off, F, iters, periodic;
+    unsigned* status;     // sticky device status bits
+};
+
+// Where Eq. PC is applied (same values as FWR_PERIODIC_* in fwr.h).
+enum : int { PERIODIC_BEFORE_EACH_FFT = 0, PERIODIC_FINAL_ONLY = 1, PERIODIC_NONE = 2 };
+
+// Status bits written by kernels.
+enum : unsigned { STATUS_NONFINITE = 1u, STATUS_TIMEOUT = 2u };
+
+// Shared-memory bytes the fused kernel needs for grid N, element T, n lenslets.
+size_t gerchberg_smem_bytes(int N, int elem_bytes, int n);
+
+// One persistent launch over all frames. Returns the launch's cudaError_t.
+cudaError_t launch_gerchberg_f32(int N, const Params<float>& p, cudaStream_t s);
+cudaError_t launch_gerchberg_f64(int N, const Params<double>& p, cudaStream_t s);
+
+// Standalone batched 2-D FFT (test entry), FP32.
+cudaError_t launch_fft2_f32(int N, const float2* in, float2* out, int F, int inverse,
+                            const float2* tw, cudaStream_t s);
+
+}  // namespace fwr

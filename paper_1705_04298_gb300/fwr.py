@@ -1,0 +1,210 @@
+"""Python binding of the C ABI in include/fwr.h (ctypes).
+
+Argument marshalling only: every step of the reconstruction runs in the CUDA
+library. PyTorch supplies device memory and streams; tensors are passed as raw
+pointers with `tensor.data_ptr()` and the current stream's handle. If the
+library has not been built this module raises on first use: there is no CPU
+fallback.
+"""
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libfwr.so")
+
+LSQ = 0
+WIENER = 1
+PERIODIC_BEFORE_EACH_FFT = 0
+PERIODIC_FINAL_ONLY = 1
+PERIODIC_NONE = 2
+OPT_PERIODIC = 1
+
+STATUS = {0: "FWR_OK", 1: "FWR_ERR_ARG", 2: "FWR_ERR_UNSUPPORTED", 3: "FWR_ERR_CUDA",
+          4: "FWR_ERR_NONFINITE", 5: "FWR_ERR_TIMEOUT"}
+
+# Every symbol include/fwr.h declares, with its ctypes signature.
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+SIGNATURES = {
+    "fwr_plan_create": (_I, [ctypes.POINTER(_P), _I, _D, _P, _I, _D, _D, _D]),
+    "fwr_plan_destroy": (None, [_P]),
+    "fwr_plan_grid": (_I, [_P]),
+    "fwr_plan_valid_count": (_I, [_P]),
+    "fwr_plan_set_option": (_I, [_P, _I, _D]),
+    "fwr_reconstruct": (_I, [_P, _P, _I, _I, _P, _P]),
+    "fwr_reconstruct_ex": (_I, [_P, _P, _P, _I, _I, _P, _P, _P]),
+    "fwr_reconstruct_f64": (_I, [_P, _P, _P, _I, _I, _P, _P, _P]),
+    "fwr_reconstruct_host": (_I, [_P, _P, _I, _I, _P, _P]),
+    "fwr_plan_reserve": (_I, [_P, _I]),
+    "fwr_fft2": (_I, [_I, _P, _P, _I, _I, _P]),
+    "fwr_get_status": (_I, [_P]),
+    "fwr_status_string": (ctypes.c_char_p, [_I]),
+    "fwr_last_error": (ctypes.c_char_p, []),
+}
+
+_lib = None
+
+
+class FwrError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        msg = "%s failed: %s" % (where, STATUS.get(code, code))
+        if code == 3 and _lib is not None:
+            msg += " (%s)" % _lib.fwr_last_error().decode()
+        super().__init__(msg)
+
+
+def load(path=LIB_PATH):
+    """Load libfwr.so and bind every declared symbol (raises if missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libfwr.so is not built (%s); run __graft_entry__.build() "
+                           "or python -m paper_1705_04298_gb300.build_lib" % path)
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(code, where):
+    if code != 0:
+        raise FwrError(code, where)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _need(t, dtype, shape, name):
+    import torch
+    if t is None:
+        return
+    if not isinstance(t, torch.Tensor) or t.dtype != dtype or tuple(t.shape) != tuple(shape):
+        raise ValueError("%s must be a %s tensor of shape %s" % (name, dtype, tuple(shape)))
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("%s must be a contiguous CUDA tensor" % name)
+
+
+class Plan:
+    """A reconstruction plan (fwr_plan_create): pupil, grid, filters.
+
+    mask: (n, n) array-like of bool; r0 and L0 in lenslet pitches.
+    """
+
+    def __init__(self, mask, pad_factor=2.0, filter=LSQ, noise_var=0.0, r0=1.0, L0=100.0,
+                 periodic=PERIODIC_BEFORE_EACH_FFT):
+        lib = load()
+        m = np.ascontiguousarray(np.asarray(mask).astype(np.uint8))
+        if m.ndim != 2 or m.shape[0] != m.shape[1]:
+            raise ValueError("mask must be square")
+        self.n = m.shape[0]
+        self._lib = lib
+        h = ctypes.c_void_p()
+        _check(lib.fwr_plan_create(ctypes.byref(h), self.n, float(pad_factor),
+                                   m.ctypes.data_as(ctypes.c_void_p), int(filter),
+                                   float(noise_var), float(r0), float(L0)), "fwr_plan_create")
+        self._h = h
+        self.N = lib.fwr_plan_grid(h)
+        self.valid_count = lib.fwr_plan_valid_count(h)
+        self.set_periodic(periodic)
+
+    def set_periodic(self, mode):
+        _check(self._lib.fwr_plan_set_option(self._h, OPT_PERIODIC, float(mode)), "fwr_plan_set_option")
+        self.periodic = mode
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.fwr_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def reconstruct(self, slopes, iters, phase=None, ext_init=None, ext_out=None, stream=None):
+        """FP32 path (fwr_reconstruct_ex). slopes: (F, 2, n, n) float32 CUDA.
+        Returns the phase tensor (F, N, N) (allocated when not given)."""
+        import torch
+        F = slopes.shape[0]
+        n, N = self.n, self.N
+        _need(slopes, torch.float32, (F, 2, n, n), "slopes")
+        if phase is None:
+            phase = torch.empty((F, N, N), dtype=torch.float32, device=slopes.device)
+        _need(phase, torch.float32, (F, N, N), "phase")
+        _need(ext_init, torch.float32, (F, 2, N, N), "ext_init")
+        _need(ext_out, torch.float32, (F, 2, N, N), "ext_out")
+        _check(self._lib.fwr_reconstruct_ex(self._h, _ptr(slopes), _ptr(ext_init), F, int(iters),
+                                            _ptr(phase), _ptr(ext_out), _stream(stream)),
+               "fwr_reconstruct_ex")
+        return phase
+
+    def reconstruct_f64(self, slopes, iters, phase=None, ext_init=None, ext_out=None, stream=None):
+        """FP64 path (fwr_reconstruct_f64), N <= 64."""
+        import torch
+        F = slopes.shape[0]
+        n, N = self.n, self.N
+        _need(slopes, torch.float64, (F, 2, n, n), "slopes")
+        if phase is None:
+            phase = torch.empty((F, N, N), dtype=torch.float64, device=slopes.device)
+        _need(phase, torch.float64, (F, N, N), "phase")
+        _need(ext_init, torch.float64, (F, 2, N, N), "ext_init")
+        _need(ext_out, torch.float64, (F, 2, N, N), "ext_out")
+        _check(self._lib.fwr_reconstruct_f64(self._h, _ptr(slopes), _ptr(ext_init), F, int(iters),
+                                             _ptr(phase), _ptr(ext_out), _stream(stream)),
+               "fwr_reconstruct_f64")
+        return phase
+
+    def reserve(self, n_frames):
+        _check(self._lib.fwr_plan_reserve(self._h, int(n_frames)), "fwr_plan_reserve")
+
+    def reconstruct_host(self, slopes_host, iters, phase_host, stream=None):
+        """End-to-end call on host tensors (pinned for asynchronous copies):
+        slopes_host (F, 2, n, n) float32 CPU, phase_host (F, N, N) float32 CPU.
+        Enqueues H2D, the reconstruction and D2H on `stream`."""
+        import torch
+        F = slopes_host.shape[0]
+        for t, shp, name in ((slopes_host, (F, 2, self.n, self.n), "slopes_host"),
+                             (phase_host, (F, self.N, self.N), "phase_host")):
+            if t.dtype != torch.float32 or tuple(t.shape) != shp or t.is_cuda or not t.is_contiguous():
+                raise ValueError("%s must be a contiguous float32 CPU tensor of shape %s" % (name, shp))
+        _check(self._lib.fwr_reconstruct_host(self._h, _ptr(slopes_host), F, int(iters),
+                                              _ptr(phase_host), _stream(stream)),
+               "fwr_reconstruct_host")
+        return phase_host
+
+    def status(self):
+        """Read and clear the sticky device status (synchronises)."""
+        return STATUS.get(self._lib.fwr_get_status(self._h))
+
+
+def fft2(x, inverse=False, out=None, stream=None):
+    """Batched 2-D FFT (fwr_fft2) of a (F, N, N) complex64 CUDA tensor; no
+    1/N^2 scaling on the inverse."""
+    import torch
+    if x.dtype != torch.complex64 or x.dim() != 3 or x.shape[1] != x.shape[2] or not x.is_cuda:
+        raise ValueError("x must be a (F, N, N) complex64 CUDA tensor")
+    x = x.contiguous()
+    if out is None:
+        out = torch.empty_like(x)
+    lib = load()
+    _check(lib.fwr_fft2(int(x.shape[1]), _ptr(x), _ptr(out), int(x.shape[0]), int(bool(inverse)),
+                        _stream(stream)), "fwr_fft2")
+    return out

@@ -1,0 +1,246 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle on the
+same seeded inputs.
+
+Tolerances (relative phase rms, piston removed, full N x N grid):
+  FP64 GPU path  <= 1e-11   (only summation order differs from the oracle)
+  FP32 GPU path  <= 1e-5    (stated target for every FP32 path)
+Index/bitwise facts (in-pupil slopes of the extended output, determinism,
+host vs device entry points) are compared exactly.
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1705_04298_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+FP32_TOL = 1e-5
+FP64_TOL = 1e-11
+
+
+@pytest.fixture(scope="module")
+def fwr():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1705_04298_gb300 import fwr as m
+    m.load()
+    return m
+
+
+def rel_rms(got, ref):
+    d = np.asarray(got, np.float64) - ref
+    d = d - d.mean()
+    r = ref - ref.mean()
+    return float(np.sqrt(np.sum(d * d) / np.sum(r * r)))
+
+
+FILTERS = {"lsq": oracle.FILTER_LSQ, "wiener": oracle.FILTER_WIENER}
+
+
+def run_oracle(slopes, mask, pad, iters, filt, noise_var, r0p, L0p, periodic, ext_init=None):
+    return oracle.reconstruct(slopes, mask, pad, iters, filt, noise_var, r0p, L0p, periodic, ext_init)
+
+
+def make_plan(fwr, mask, pad, filt, noise_var=0.0, r0p=1.0, L0p=100.0, periodic=0):
+    return fwr.Plan(mask, pad, filt, noise_var, r0p, L0p, periodic)
+
+
+# --------------------------------------------------------------- FFT ------
+
+@pytest.mark.parametrize("N", [16, 32, 64, 128])
+@pytest.mark.parametrize("inverse", [False, True])
+def test_fft2_matches_numpy(fwr, N, inverse):
+    rng = np.random.Generator(np.random.PCG64(N + inverse))
+    F = 7
+    x = rng.standard_normal((F, N, N)) + 1j * rng.standard_normal((F, N, N))
+    xt = torch.tensor(x.astype(np.complex64), device="cuda")
+    y = fwr.fft2(xt, inverse=inverse).cpu().numpy().astype(np.complex128)
+    ref = np.fft.ifft2(x) * N * N if inverse else np.fft.fft2(x)
+    err = np.sqrt(np.sum(np.abs(y - ref) ** 2) / np.sum(np.abs(ref) ** 2))
+    assert err < 2e-7 * math.log2(N * N)
+
+
+# ------------------------------------------------ 16x16 -> 32^2 (1 frame) -
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_small_config_lsq_k10(fwr, precision):
+    """16x16 lenslets, 32^2 grid, sigma = 0.05 rad, LSQ, 10 iterations."""
+    n, pad, k = 16, 2.0, 10
+    fr = synth.frame(n, 0, 0.05)
+    ref, ref_ext = run_oracle(fr["slopes"], fr["mask"], pad, k, oracle.FILTER_LSQ, 0.0, 1.0, 1.0,
+                              oracle.PERIODIC_BEFORE_EACH_FFT)
+    plan = make_plan(fwr, fr["mask"], pad, fwr.LSQ)
+    N = plan.N
+    if precision == "fp64":
+        s = torch.tensor(fr["slopes"][None], dtype=torch.float64, device="cuda")
+        ext = torch.empty((1, 2, N, N), dtype=torch.float64, device="cuda")
+        ph = plan.reconstruct_f64(s, k, ext_out=ext)
+        tol = FP64_TOL
+    else:
+        s = torch.tensor(fr["slopes"][None], dtype=torch.float32, device="cuda")
+        ext = torch.empty((1, 2, N, N), dtype=torch.float32, device="cuda")
+        ph = plan.reconstruct(s, k, ext_out=ext)
+        tol = FP32_TOL
+    torch.cuda.synchronize()
+    assert rel_rms(ph[0].cpu().numpy(), ref) <= tol
+    e = ext[0].cpu().numpy().astype(np.float64)
+    assert rel_rms(e, ref_ext) <= tol * 10
+    # in-pupil slopes are the measurement (bitwise in the path's precision)
+    s0x, s0y, P = oracle.embed(fr["slopes"], fr["mask"], N)
+    dt = np.float64 if precision == "fp64" else np.float32
+    assert np.array_equal(e[0][P].astype(dt), s0x[P].astype(dt))
+    assert np.array_equal(e[1][P].astype(dt), s0y[P].astype(dt))
+    assert plan.status() == "FWR_OK"
+
+
+# --------------------------------------- periodic modes x filters (N=64) --
+
+@pytest.mark.parametrize("periodic", [0, 1, 2])
+@pytest.mark.parametrize("filt", ["lsq", "wiener"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_modes_and_filters(fwr, periodic, filt, precision):
+    n, pad, k, sigma = 30, 2.0, 3, 0.1
+    r0p, L0p = synth.pitch_units(n, 0.15, 25.0)
+    F = 3
+    sl, _, mask = synth.batch(n, F, 77, sigma)
+    plan = make_plan(fwr, mask, pad, fwr.WIENER if filt == "wiener" else fwr.LSQ, sigma ** 2, r0p, L0p,
+                     periodic)
+    dtype = torch.float64 if precision == "fp64" else torch.float32
+    s = torch.tensor(sl, dtype=dtype, device="cuda")
+    ph = (plan.reconstruct_f64 if precision == "fp64" else plan.reconstruct)(s, k)
+    ph = ph.cpu().numpy()
+    tol = FP64_TOL if precision == "fp64" else FP32_TOL
+    for f in range(F):
+        ref, _ = run_oracle(sl[f], mask, pad, k, FILTERS[filt], sigma ** 2, r0p, L0p, periodic)
+        assert rel_rms(ph[f], ref) <= tol, (f, rel_rms(ph[f], ref))
+
+
+# ------------------------------ 40x40 -> 128^2, Wiener, every k, tail ------
+
+@pytest.mark.parametrize("k", [0, 1, 2, 5, 10])
+def test_40x40_wiener_iterations(fwr, k):
+    n, pad = 40, 3.2
+    r0p, L0p = synth.pitch_units(n, 0.15, 25.0)
+    sig = [0.02, 0.1]
+    F = 4
+    sl, _, mask = synth.batch(n, F, 1000, sig)
+    for s_i in sig:
+        plan = make_plan(fwr, mask, pad, fwr.WIENER, s_i ** 2, r0p, L0p)
+        assert plan.N == 128
+        ph = plan.reconstruct(torch.tensor(sl, dtype=torch.float32, device="cuda"), k).cpu().numpy()
+        for f in range(F):
+            ref, _ = run_oracle(sl[f], mask, pad, k, oracle.FILTER_WIENER, s_i ** 2, r0p, L0p, 0)
+            assert rel_rms(ph[f], ref) <= FP32_TOL, (k, s_i, f, rel_rms(ph[f], ref))
+
+
+def test_persistent_tail_frames(fwr):
+    """More frames than resident CTAs: every CTA loops, the last ones partly."""
+    n, pad, k = 40, 3.2, 2
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    F = sms + 9
+    sl, _, mask = synth.batch(n, F, 4242, 0.05)
+    plan = make_plan(fwr, mask, pad, fwr.LSQ)
+    ph = plan.reconstruct(torch.tensor(sl, dtype=torch.float32, device="cuda"), k).cpu().numpy()
+    for f in [0, 1, sms - 1, sms, sms + 8]:
+        ref, _ = run_oracle(sl[f], mask, pad, k, oracle.FILTER_LSQ, 0.0, 1.0, 1.0, 0)
+        assert rel_rms(ph[f], ref) <= FP32_TOL, f
+
+
+def test_full_size_40x40_1000_frames_sampled(fwr):
+    """The benchmarked launch (1000 frames, k = 10, Wiener): sampled frames
+    against the oracle, every frame for zero mean and finiteness."""
+    n, pad, k, F, sigma = 40, 3.2, 10, 1000, 0.02
+    r0p, L0p = synth.pitch_units(n, 0.15, 25.0)
+    sl, _, mask = synth.batch(n, F, 1000, [0.02, 0.1])
+    plan = make_plan(fwr, mask, pad, fwr.WIENER, sigma ** 2, r0p, L0p)
+    ph = plan.reconstruct(torch.tensor(sl, dtype=torch.float32, device="cuda"), k)
+    torch.cuda.synchronize()
+    assert torch.isfinite(ph).all()
+    means = ph.double().mean(dim=(1, 2)).abs().max().item()
+    assert means < 1e-4 * ph.double().std().item()
+    phn = ph.cpu().numpy()
+    for f in [0, 1, 499, 998, 999]:
+        ref, _ = run_oracle(sl[f], mask, pad, k, oracle.FILTER_WIENER, sigma ** 2, r0p, L0p, 0)
+        assert rel_rms(phn[f], ref) <= FP32_TOL, f
+
+
+# ---------------------------------------------------- warm start / extras -
+
+def test_warm_start_and_invariants(fwr):
+    n, pad, k = 16, 2.0, 4
+    F = 3
+    sl, _, mask = synth.batch(n, F, 91, 0.05)
+    N = 32
+    rng = np.random.Generator(np.random.PCG64(5))
+    ext_init = rng.standard_normal((F, 2, N, N))
+    plan = make_plan(fwr, mask, pad, fwr.LSQ)
+    ext_out = torch.empty((F, 2, N, N), dtype=torch.float64, device="cuda")
+    ph = plan.reconstruct_f64(torch.tensor(sl, device="cuda"), k,
+                              ext_init=torch.tensor(ext_init, device="cuda"), ext_out=ext_out)
+    ph = ph.cpu().numpy()
+    eo = ext_out.cpu().numpy()
+    for f in range(F):
+        ref, ref_ext = run_oracle(sl[f], mask, pad, k, oracle.FILTER_LSQ, 0.0, 1.0, 1.0, 0, ext_init[f])
+        assert rel_rms(ph[f], ref) <= FP64_TOL
+        assert np.max(np.abs(eo[f] - ref_ext)) <= 1e-10 * np.max(np.abs(ref_ext))
+        # Eq. PC: zero row sums of x slopes, zero column sums of y slopes
+        assert np.max(np.abs(eo[f][0].sum(axis=1))) <= 1e-10
+        assert np.max(np.abs(eo[f][1].sum(axis=0))) <= 1e-10
+
+
+def test_zero_frames_and_argument_errors(fwr):
+    mask = synth.pupil_mask(16)
+    plan = make_plan(fwr, mask, 2.0, fwr.LSQ)
+    s = torch.zeros((0, 2, 16, 16), dtype=torch.float32, device="cuda")
+    plan.reconstruct(s, 3)
+    with pytest.raises(fwr.FwrError):
+        plan.reconstruct(torch.zeros((1, 2, 16, 16), device="cuda"), 65)
+    with pytest.raises(fwr.FwrError):
+        plan.set_periodic(3)
+    big = make_plan(fwr, synth.pupil_mask(40), 3.2, fwr.LSQ)
+    with pytest.raises(fwr.FwrError):
+        big.reconstruct_f64(torch.zeros((1, 2, 40, 40), dtype=torch.float64, device="cuda"), 1)
+
+
+def test_extreme_pupil_sizes(fwr):
+    # smallest lenslet array, and the largest n that still leaves the fill
+    # row/column outside the pupil (n = N - 2)
+    for n, pad in [(2, 8.0), (30, 32 / 30)]:
+        mask = synth.pupil_mask(n) if n > 2 else np.ones((2, 2), bool)
+        sl, _, _ = synth.batch(n, 2, 31, 0.05)
+        sl = np.where(mask[None, None], sl, 0.0)
+        plan = make_plan(fwr, mask, pad, fwr.LSQ)
+        ph = plan.reconstruct_f64(torch.tensor(sl, device="cuda"), 3).cpu().numpy()
+        for f in range(2):
+            ref, _ = run_oracle(sl[f], mask, pad, 3, oracle.FILTER_LSQ, 0.0, 1.0, 1.0, 0)
+            assert rel_rms(ph[f], ref) <= FP64_TOL, (n, f)
+
+
+def test_nonfinite_input_sets_status(fwr):
+    mask = synth.pupil_mask(16)
+    plan = make_plan(fwr, mask, 2.0, fwr.LSQ)
+    sl, _, _ = synth.batch(16, 2, 5, 0.05)
+    sl[1, 0, 8, 8] = np.nan
+    plan.reconstruct(torch.tensor(sl, dtype=torch.float32, device="cuda"), 1)
+    assert plan.status() == "FWR_ERR_NONFINITE"
+    assert plan.status() == "FWR_OK"  # read-and-clear
+
+
+def test_deterministic_and_host_path_identical(fwr):
+    n, pad, k, F = 40, 3.2, 5, 64
+    sl, _, mask = synth.batch(n, F, 3, 0.05)
+    plan = make_plan(fwr, mask, pad, fwr.LSQ)
+    s = torch.tensor(sl, dtype=torch.float32, device="cuda")
+    a = plan.reconstruct(s, k).cpu()
+    b = plan.reconstruct(s, k).cpu()
+    assert torch.equal(a, b)
+    sh = torch.tensor(sl, dtype=torch.float32).pin_memory()
+    out = torch.empty((F, plan.N, plan.N), dtype=torch.float32).pin_memory()
+    plan.reconstruct_host(sh, k, out)
+    torch.cuda.synchronize()
+    assert torch.equal(out, a)
