@@ -68,7 +68,7 @@ TRAFFIC = {}
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("fwr_gerchberg.cu", "fwr_internal.h"):
+    for f in ("fwr_fused.cu", "fwr_fft.cuh", "fwr_internal.h"):
         with open(os.path.join(ROOT, "paper_1705_04298_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -93,7 +93,7 @@ class ClockSampler:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=self.fh, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
@@ -221,7 +221,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -326,7 +326,7 @@ def main():
                        "valid_lenslets": plan.valid_count, "parallelism": "replicas (frames sharded)"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": TRAFFIC.get(src),
-                         "kernel": "gerchberg_kernel<float,128>", "flops_per_launch": fl,
+                         "kernel": "fused_kernel<float,128>", "flops_per_launch": fl,
                          "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 x 2.07 GHz (max SM clock)",
                          "source_hash": src},
             "e2e": {"value": FRAMES * world / (e2e_step / 1000.0), "unit": "frames/s",

@@ -1,6 +1,7 @@
 // C ABI of the reconstructor (declared in include/fwr.h): argument checks, the
 // FP64 filter builder and plan-owned device tables. Every step of the
-// reconstruction itself runs in the kernels of fwr_gerchberg.cu.
+// reconstruction itself runs in the kernels of fwr_fused.cu (main path) and
+// fwr_basic.cu (generic fallback for pupils too large for the main layout).
 
 #include <cuda_runtime.h>
 
@@ -33,6 +34,7 @@ template <typename T> struct DevTables {
     V* tw = nullptr;
     V* A = nullptr;
     V* Tt = nullptr;
+    T* pt = nullptr;
     T* iota = nullptr;
     T* wfin = nullptr;
 };
@@ -41,6 +43,7 @@ template <typename T> void free_tables(DevTables<T>& t) {
     cudaFree(t.tw);
     cudaFree(t.A);
     cudaFree(t.Tt);
+    cudaFree(t.pt);
     cudaFree(t.iota);
     cudaFree(t.wfin);
     t = DevTables<T>();
@@ -78,6 +81,7 @@ double sinc(double x) { return x == 0.0 ? 1.0 : std::sin(kPi * x) / (kPi * x); }
 // weight of Eq. 3). Returned in the device layout of fwr::Tables.
 struct HostTables {
     std::vector<double> tw, A, Tt;  // interleaved re, im; N entries each
+    std::vector<double> pt;         // [N][4]: p = a conj(T) (re, im), |a|^2, |T|^2
     std::vector<double> iota, wfin; // (N/2+1) * N
 };
 
@@ -102,6 +106,14 @@ HostTables build_tables(int N, int filter, double noise_var, double r0, double L
         const double s = sinc(u);
         h.Tt[2 * j] = (j == N / 2) ? 0.0 : s * std::cos(kPi * u);
         h.Tt[2 * j + 1] = (j == N / 2) ? 0.0 : s * std::sin(kPi * u);
+    }
+    h.pt.resize(4 * size_t(N));
+    for (int j = 0; j < N; ++j) {
+        const double ar = h.A[2 * j], ai = h.A[2 * j + 1], tr = h.Tt[2 * j], ti = h.Tt[2 * j + 1];
+        h.pt[4 * j] = ar * tr + ai * ti;      // Re a conj(T)
+        h.pt[4 * j + 1] = ai * tr - ar * ti;  // Im a conj(T)
+        h.pt[4 * j + 2] = ar * ar + ai * ai;
+        h.pt[4 * j + 3] = tr * tr + ti * ti;
     }
     const int H = N / 2;
     h.iota.assign(size_t(H + 1) * N, 0.0);
@@ -137,7 +149,9 @@ template <typename T>
 fwr_status upload_tables(const HostTables& h, int N, DevTables<T>& d) {
     typedef typename fwr::cvec<T>::type V;
     const int H = N / 2;
-    std::vector<T> tw(2 * N), A(2 * N), Tt(2 * N), iota(size_t(H + 1) * N), wfin(size_t(H + 1) * N);
+    std::vector<T> tw(2 * N), A(2 * N), Tt(2 * N), pt(4 * size_t(N)), iota(size_t(H + 1) * N),
+        wfin(size_t(H + 1) * N);
+    for (int i = 0; i < 4 * N; ++i) pt[i] = T(h.pt[i]);
     for (int i = 0; i < 2 * N; ++i) {
         tw[i] = T(h.tw[i]);
         A[i] = T(h.A[i]);
@@ -151,11 +165,13 @@ fwr_status upload_tables(const HostTables& h, int N, DevTables<T>& d) {
     if ((e = cudaMalloc(&d.tw, N * sizeof(V))) != cudaSuccess) return cuda_fail(e, "cudaMalloc tables");
     if ((e = cudaMalloc(&d.A, N * sizeof(V))) != cudaSuccess) return cuda_fail(e, "cudaMalloc tables");
     if ((e = cudaMalloc(&d.Tt, N * sizeof(V))) != cudaSuccess) return cuda_fail(e, "cudaMalloc tables");
+    if ((e = cudaMalloc(&d.pt, pt.size() * sizeof(T))) != cudaSuccess) return cuda_fail(e, "cudaMalloc tables");
     if ((e = cudaMalloc(&d.iota, iota.size() * sizeof(T))) != cudaSuccess) return cuda_fail(e, "cudaMalloc tables");
     if ((e = cudaMalloc(&d.wfin, wfin.size() * sizeof(T))) != cudaSuccess) return cuda_fail(e, "cudaMalloc tables");
     if ((e = cudaMemcpy(d.tw, tw.data(), N * sizeof(V), cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(d.A, A.data(), N * sizeof(V), cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(d.Tt, Tt.data(), N * sizeof(V), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(d.pt, pt.data(), pt.size() * sizeof(T), cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(d.iota, iota.data(), iota.size() * sizeof(T), cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(d.wfin, wfin.data(), wfin.size() * sizeof(T), cudaMemcpyHostToDevice)) != cudaSuccess)
         return cuda_fail(e, "cudaMemcpy tables");
@@ -168,6 +184,7 @@ fwr::Tables<T> view(const DevTables<T>& d) {
     t.tw = d.tw;
     t.A = d.A;
     t.Tt = d.Tt;
+    t.pt = d.pt;
     t.iota = d.iota;
     t.wfin = d.wfin;
     return t;
@@ -290,7 +307,9 @@ fwr_status fwr_reconstruct_ex(fwr_plan* p, const float* slopes, const float* ext
     k.iters = iters;
     k.periodic = p->periodic;
     k.status = p->d_status;
-    cudaError_t e = fwr::launch_gerchberg_f32(p->N, k, static_cast<cudaStream_t>(stream));
+    cudaError_t e = fwr::fused_supported(p->N, 4, p->n)
+                        ? fwr::launch_fused_f32(p->N, k, static_cast<cudaStream_t>(stream))
+                        : fwr::launch_basic_f32(p->N, k, static_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? FWR_OK : cuda_fail(e, "gerchberg launch");
 }
 
@@ -318,7 +337,9 @@ fwr_status fwr_reconstruct_f64(fwr_plan* p, const double* slopes, const double* 
     k.iters = iters;
     k.periodic = p->periodic;
     k.status = p->d_status;
-    cudaError_t e = fwr::launch_gerchberg_f64(p->N, k, static_cast<cudaStream_t>(stream));
+    cudaError_t e = fwr::fused_supported(p->N, 8, p->n)
+                        ? fwr::launch_fused_f64(p->N, k, static_cast<cudaStream_t>(stream))
+                        : fwr::launch_basic_f64(p->N, k, static_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? FWR_OK : cuda_fail(e, "gerchberg f64 launch");
 }
 

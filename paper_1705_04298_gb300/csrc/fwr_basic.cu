@@ -1,4 +1,5 @@
-// Fused persistent Gerchberg kernel for sm_103a.
+// Generic fused Gerchberg kernel for sm_103a (fallback for pupils too large for
+// the shared-memory layout of fwr_fused.cu, and the FFT test entry).
 //
 // One CTA owns one frame at a time and keeps the frame's whole N x N complex
 // grid Z = sx + i sy in shared memory for all iterations of Algorithm 1
@@ -25,72 +26,7 @@
 
 namespace fwr {
 
-#include "fwr_w32.inc"
-
-// ---------------------------------------------------------------------------
-// complex helpers
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ float2 mk(float a, float b) { return make_float2(a, b); }
-__device__ __forceinline__ double2 mk(double a, double b) { return make_double2(a, b); }
-template <typename V> __device__ __forceinline__ V cadd(V a, V b) { return mk(a.x + b.x, a.y + b.y); }
-template <typename V> __device__ __forceinline__ V csub(V a, V b) { return mk(a.x - b.x, a.y - b.y); }
-template <typename V> __device__ __forceinline__ V cmul(V a, V b) {
-    return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-// conj(a) * b
-template <typename V> __device__ __forceinline__ V cmulc(V a, V b) {
-    return mk(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
-}
-__device__ __forceinline__ float2 w32(float2, int i) { return c_w32f[i]; }
-__device__ __forceinline__ double2 w32(double2, int i) { return c_w32d[i]; }
-
-// d * w_32^idx (forward) or d * conj(w_32^idx) (inverse); idx is a
-// compile-time constant after unrolling, so the trivial cases fold away and
-// the rest read the constant bank directly.
-template <bool INV, typename V>
-__device__ __forceinline__ V tw32(V d, int idx) {
-    if (idx == 0) return d;
-    if (idx == 8) return INV ? mk(-d.y, d.x) : mk(d.y, -d.x);
-    if (idx == 16) return mk(-d.x, -d.y);
-    if (idx == 24) return INV ? mk(d.y, -d.x) : mk(-d.y, d.x);
-    V w = w32(d, idx);
-    if (INV) w.y = -w.y;
-    return cmul(d, w);
-}
-
-template <int R> struct Log2 { static constexpr int v = 1 + Log2<R / 2>::v; };
-template <> struct Log2<1> { static constexpr int v = 0; };
-
-__host__ __device__ constexpr int bitrev(int i, int bits) {
-    int r = 0;
-    for (int b = 0; b < bits; ++b) r |= ((i >> b) & 1) << (bits - 1 - b);
-    return r;
-}
-
-// In-register R-point DFT (R <= 32), radix-2 decimation in frequency, output
-// reordered to natural order (a register renaming after unrolling).
-template <int R, bool INV, typename V>
-__device__ __forceinline__ void dft_reg(V* x) {
-    constexpr int L = Log2<R>::v;
-#pragma unroll
-    for (int s = 0; s < L; ++s) {
-        const int h = R >> (s + 1);
-#pragma unroll
-        for (int b = 0; b < R; b += 2 * h) {
-#pragma unroll
-            for (int j = 0; j < h; ++j) {
-                V a = x[b + j], c = x[b + j + h];
-                x[b + j] = cadd(a, c);
-                x[b + j + h] = tw32<INV>(csub(a, c), j * (32 / (2 * h)));
-            }
-        }
-    }
-    V y[R];
-#pragma unroll
-    for (int i = 0; i < R; ++i) y[i] = x[bitrev(i, L)];
-#pragma unroll
-    for (int i = 0; i < R; ++i) x[i] = y[i];
-}
+#include "fwr_fft.cuh"
 
 template <int N> struct Split;
 template <> struct Split<16> { static constexpr int R1 = 4, R2 = 4, NT = 64; };
@@ -212,11 +148,6 @@ __device__ __forceinline__ void spectral(V* Z, const V* A, const V* Tt, const T*
     }
 }
 
-template <typename T> __device__ __forceinline__ T warp_sum(T v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
 
 // Eq. PC: Z.x[m][N-1] = -sum_{c<N-1} Z.x[m][c]; Z.y[N-1][c] = -sum_{m<N-1} Z.y[m][c].
 // The x and y fills touch different components, so they run together.
@@ -267,7 +198,7 @@ __host__ __device__ constexpr size_t smem_layout_bytes(int n) {
 
 template <typename T, int N>
 __global__ void __launch_bounds__(Split<N>::NT)
-gerchberg_kernel(Params<T> p) {
+basic_kernel(Params<T> p) {
     typedef typename cvec<T>::type V;
     constexpr int NT = Split<N>::NT, S = N + 1, H = N / 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -350,7 +281,7 @@ gerchberg_kernel(Params<T> p) {
     if (threadIdx.x == 0 && s_bad) atomicOr(p.status, STATUS_NONFINITE);
 }
 
-size_t gerchberg_smem_bytes(int N, int elem_bytes, int n) {
+size_t basic_smem_bytes(int N, int elem_bytes, int n) {
     const bool d = elem_bytes == 8;
     switch (N) {
         case 16: return d ? smem_layout_bytes<double, 16>(n) : smem_layout_bytes<float, 16>(n);
@@ -365,7 +296,7 @@ template <typename T, int N>
 static cudaError_t launch_one(const Params<T>& p, cudaStream_t s) {
     constexpr int NT = Split<N>::NT;
     const size_t smem = smem_layout_bytes<T, N>(p.n);
-    auto kern = gerchberg_kernel<T, N>;
+    auto kern = basic_kernel<T, N>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per_sm = 0;
@@ -379,7 +310,7 @@ static cudaError_t launch_one(const Params<T>& p, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_gerchberg_f32(int N, const Params<float>& p, cudaStream_t s) {
+cudaError_t launch_basic_f32(int N, const Params<float>& p, cudaStream_t s) {
     switch (N) {
         case 16: return launch_one<float, 16>(p, s);
         case 32: return launch_one<float, 32>(p, s);
@@ -389,60 +320,11 @@ cudaError_t launch_gerchberg_f32(int N, const Params<float>& p, cudaStream_t s) 
     }
 }
 
-cudaError_t launch_gerchberg_f64(int N, const Params<double>& p, cudaStream_t s) {
+cudaError_t launch_basic_f64(int N, const Params<double>& p, cudaStream_t s) {
     switch (N) {
         case 16: return launch_one<double, 16>(p, s);
         case 32: return launch_one<double, 32>(p, s);
         case 64: return launch_one<double, 64>(p, s);
-        default: return cudaErrorInvalidValue;
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Standalone batched 2-D FFT (test entry for the transform used above).
-// ---------------------------------------------------------------------------
-template <int N, bool INV>
-__global__ void __launch_bounds__(Split<N>::NT)
-fft2_kernel(const float2* in, float2* out, int F, const float2* twg) {
-    constexpr int NT = Split<N>::NT, S = N + 1;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    float2* Z = reinterpret_cast<float2*>(smem_raw);
-    float2* tw = Z + N * S;
-    for (int i = threadIdx.x; i < N; i += NT) tw[i] = twg[i];
-    for (int f = blockIdx.x; f < F; f += gridDim.x) {
-        const float2* src = in + size_t(f) * N * N;
-        for (int idx = threadIdx.x; idx < N * N; idx += NT) Z[(idx / N) * S + idx % N] = src[idx];
-        __syncthreads();
-        fft2<N, NT, INV>(Z, tw);
-        float2* dst = out + size_t(f) * N * N;
-        for (int idx = threadIdx.x; idx < N * N; idx += NT) dst[idx] = Z[(idx / N) * S + idx % N];
-        __syncthreads();
-    }
-}
-
-template <int N>
-static cudaError_t launch_fft2_n(const float2* in, float2* out, int F, int inverse, const float2* tw,
-                                 cudaStream_t s) {
-    constexpr int NT = Split<N>::NT;
-    const size_t smem = (size_t(N) * (N + 1) + N) * sizeof(float2);
-    auto kern = inverse ? fft2_kernel<N, true> : fft2_kernel<N, false>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0;
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    int grid = F < sms * 4 ? F : sms * 4;
-    kern<<<grid, NT, smem, s>>>(in, out, F, tw);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_fft2_f32(int N, const float2* in, float2* out, int F, int inverse, const float2* tw,
-                            cudaStream_t s) {
-    switch (N) {
-        case 16: return launch_fft2_n<16>(in, out, F, inverse, tw, s);
-        case 32: return launch_fft2_n<32>(in, out, F, inverse, tw, s);
-        case 64: return launch_fft2_n<64>(in, out, F, inverse, tw, s);
-        case 128: return launch_fft2_n<128>(in, out, F, inverse, tw, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -18,6 +18,7 @@ template <typename T> struct Tables {
     const typename cvec<T>::type* tw;  // [N]   e^{-2 i pi j / N}
     const typename cvec<T>::type* A;   // [N]   a(u) = e^{2 i pi u} - 1
     const typename cvec<T>::type* Tt;  // [N]   T(u) = sinc(u) e^{i pi u}, 0 at u = -1/2
+    const T* pt;                       // [N][4]  p(u) = a(u) conj(T(u)) (re, im), |a(u)|^2, |T(u)|^2
     const T* iota;                     // [(N/2+1) N] 1/|G|^2 / N^2 (0 at nulls)
     const T* wfin;                     // [(N/2+1) N] final weight / N^2 (LSQ or Wiener)
 };
@@ -39,12 +40,18 @@ enum : int { PERIODIC_BEFORE_EACH_FFT = 0, PERIODIC_FINAL_ONLY = 1, PERIODIC_NON
 // Status bits written by kernels.
 enum : unsigned { STATUS_NONFINITE = 1u, STATUS_TIMEOUT = 2u };
 
-// Shared-memory bytes the fused kernel needs for grid N, element T, n lenslets.
-size_t gerchberg_smem_bytes(int N, int elem_bytes, int n);
+// Shared-memory bytes of the generic kernel (fwr_basic.cu) for grid N.
+size_t basic_smem_bytes(int N, int elem_bytes, int n);
 
-// One persistent launch over all frames. Returns the launch's cudaError_t.
-cudaError_t launch_gerchberg_f32(int N, const Params<float>& p, cudaStream_t s);
-cudaError_t launch_gerchberg_f64(int N, const Params<double>& p, cudaStream_t s);
+// Generic kernel (fwr_basic.cu): one persistent launch over all frames.
+cudaError_t launch_basic_f32(int N, const Params<float>& p, cudaStream_t s);
+cudaError_t launch_basic_f64(int N, const Params<double>& p, cudaStream_t s);
+
+// Main fused kernel (fwr_fused.cu). fused_supported() says whether its
+// shared-memory layout fits grid N with n lenslets for the element size.
+bool fused_supported(int N, int elem_bytes, int n);
+cudaError_t launch_fused_f32(int N, const Params<float>& p, cudaStream_t s);
+cudaError_t launch_fused_f64(int N, const Params<double>& p, cudaStream_t s);
 
 // Standalone batched 2-D FFT (test entry), FP32.
 cudaError_t launch_fft2_f32(int N, const float2* in, float2* out, int F, int inverse,
