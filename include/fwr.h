@@ -122,13 +122,16 @@ fwr_status fwr_plan_set_option(fwr_plan* plan, int key, double value);
  *   iters       Gerchberg iterations, 0 <= iters <= 64 (0 = zero padding,
  *               plus the periodic fill where the option asks for it)
  *   phase_dev   [n_frames][N][N] float output, radians, zero mean
- * n_frames = 0 is a no-op. All work is one persistent kernel launch.
+ * n_frames = 0 is a no-op. All work is one persistent kernel launch. For
+ * N = 256 the grid of each frame is streamed through shared memory from a
+ * plan-owned global scratch area (one 512 KB area per SM, allocated by
+ * fwr_plan_create), so two calls on one plan must not run concurrently.
  */
 fwr_status fwr_reconstruct(fwr_plan* plan, const float* slopes_dev, int n_frames, int iters,
                            float* phase_dev, void* stream);
 
 /*
- * As fwr_reconstruct, with two optional extras.
+ * As fwr_reconstruct, with two optional extras (ext_out needs N <= 128).
  *   ext_init_dev  [n_frames][2][N][N] initial slopes used OUTSIDE the pupil
  *                 before the first iteration (a warm start), or NULL for 0
  *   phase_dev     may be NULL (no final reconstruction)

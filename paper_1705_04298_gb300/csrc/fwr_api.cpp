@@ -59,6 +59,9 @@ struct fwr_plan {
     unsigned* d_status = nullptr;
     DevTables<float> f32;
     DevTables<double> f64;
+    // 256^2 grids: per-CTA global scratch of the slab kernel
+    float2* d_scratch = nullptr;
+    int scratch_ctas = 0;
     // host-path staging
     float* d_stage_in = nullptr;
     float* d_stage_out = nullptr;
@@ -190,7 +193,7 @@ fwr::Tables<T> view(const DevTables<T>& d) {
     return t;
 }
 
-bool supported_grid(int N) { return N == 16 || N == 32 || N == 64 || N == 128; }
+bool supported_grid(int N) { return N == 16 || N == 32 || N == 64 || N == 128 || N == 256; }
 
 }  // namespace
 
@@ -243,6 +246,15 @@ fwr_status fwr_plan_create(fwr_plan** out, int n, double pad_factor, const uint8
         st = upload_tables<float>(h, N, p->f32);
         if (st == FWR_OK && N <= 64) st = upload_tables<double>(h, N, p->f64);
     }
+    if (st == FWR_OK && N == 256) {
+        if (fwr::slab_smem_bytes(n) > size_t(227) * 1024) {
+            st = FWR_ERR_UNSUPPORTED;
+        } else {
+            p->scratch_ctas = fwr::slab_max_ctas();
+            const size_t b = size_t(p->scratch_ctas) * fwr::slab_scratch_elems_per_cta() * sizeof(float2);
+            if ((e = cudaMalloc(&p->d_scratch, b)) != cudaSuccess) st = cuda_fail(e, "cudaMalloc scratch");
+        }
+    }
     if (st != FWR_OK) {
         fwr_plan_destroy(p);
         return st;
@@ -260,6 +272,7 @@ void fwr_plan_destroy(fwr_plan* p) {
     free_tables(p->f64);
     cudaFree(p->d_mask);
     cudaFree(p->d_status);
+    cudaFree(p->d_scratch);
     cudaFree(p->d_stage_in);
     cudaFree(p->d_stage_out);
     cudaSetDevice(prev);
@@ -307,9 +320,14 @@ fwr_status fwr_reconstruct_ex(fwr_plan* p, const float* slopes, const float* ext
     k.iters = iters;
     k.periodic = p->periodic;
     k.status = p->d_status;
-    cudaError_t e = fwr::fused_supported(p->N, 4, p->n)
-                        ? fwr::launch_fused_f32(p->N, k, static_cast<cudaStream_t>(stream))
-                        : fwr::launch_basic_f32(p->N, k, static_cast<cudaStream_t>(stream));
+    cudaError_t e;
+    if (p->N == 256) {
+        if (ext_out || !phase) return FWR_ERR_UNSUPPORTED;
+        e = fwr::launch_slab(k, p->d_scratch, p->scratch_ctas, static_cast<cudaStream_t>(stream));
+    } else {
+        e = fwr::fused_supported(p->N, 4, p->n) ? fwr::launch_fused_f32(p->N, k, static_cast<cudaStream_t>(stream))
+                                                : fwr::launch_basic_f32(p->N, k, static_cast<cudaStream_t>(stream));
+    }
     return e == cudaSuccess ? FWR_OK : cuda_fail(e, "gerchberg launch");
 }
 

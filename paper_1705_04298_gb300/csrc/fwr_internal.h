@@ -47,6 +47,14 @@ size_t basic_smem_bytes(int N, int elem_bytes, int n);
 cudaError_t launch_basic_f32(int N, const Params<float>& p, cudaStream_t s);
 cudaError_t launch_basic_f64(int N, const Params<double>& p, cudaStream_t s);
 
+// 256^2 grids (fwr_slab.cu): the grid lives in a per-CTA global scratch area
+// of slab_scratch_elems_per_cta() float2 and is streamed through shared
+// memory. launch_slab uses at most max_ctas CTAs (scratch must hold that many).
+size_t slab_smem_bytes(int n);
+size_t slab_scratch_elems_per_cta();
+int slab_max_ctas();
+cudaError_t launch_slab(const Params<float>& p, float2* scratch, int max_ctas, cudaStream_t s);
+
 // Main fused kernel (fwr_fused.cu). fused_supported() says whether its
 // shared-memory layout fits grid N with n lenslets for the element size.
 bool fused_supported(int N, int elem_bytes, int n);

@@ -244,3 +244,43 @@ def test_deterministic_and_host_path_identical(fwr):
     plan.reconstruct_host(sh, k, out)
     torch.cuda.synchronize()
     assert torch.equal(out, a)
+
+
+# ------------------------------------------- 256^2 grids (slab kernel) ----
+
+@pytest.mark.parametrize("n,pad,k,periodic,filt", [
+    (80, 3.2, 5, 0, "lsq"),
+    (128, 2.0, 2, 1, "wiener"),
+    (80, 3.2, 0, 0, "wiener"),
+    (100, 2.56, 3, 2, "lsq"),
+])
+def test_256_grid(fwr, n, pad, k, periodic, filt):
+    r0p, L0p = synth.pitch_units(n, 0.15, 25.0)
+    sigma = 0.05
+    F = 3
+    sl, _, mask = synth.batch(n, F, 2000 + n, sigma)
+    plan = make_plan(fwr, mask, pad, fwr.WIENER if filt == "wiener" else fwr.LSQ, sigma ** 2, r0p, L0p,
+                     periodic)
+    assert plan.N == 256
+    ph = plan.reconstruct(torch.tensor(sl, dtype=torch.float32, device="cuda"), k).cpu().numpy()
+    for f in range(F):
+        ref, _ = run_oracle(sl[f], mask, pad, k, FILTERS[filt], sigma ** 2, r0p, L0p, periodic)
+        assert rel_rms(ph[f], ref) <= FP32_TOL, (f, rel_rms(ph[f], ref))
+
+
+def test_256_grid_persistent_tail_and_limits(fwr):
+    n, pad, k = 80, 3.2, 1
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    F = sms + 5
+    sl, _, mask = synth.batch(n, F, 77, 0.05)
+    plan = make_plan(fwr, mask, pad, fwr.LSQ)
+    ph = plan.reconstruct(torch.tensor(sl, dtype=torch.float32, device="cuda"), k).cpu().numpy()
+    for f in [0, sms, sms + 4]:
+        ref, _ = run_oracle(sl[f], mask, pad, k, oracle.FILTER_LSQ, 0.0, 1.0, 1.0, 0)
+        assert rel_rms(ph[f], ref) <= FP32_TOL, f
+    # 256^2: FP32 only, no extended-slope output
+    with pytest.raises(fwr.FwrError):
+        plan.reconstruct_f64(torch.zeros((1, 2, n, n), dtype=torch.float64, device="cuda"), 1)
+    with pytest.raises(fwr.FwrError):
+        plan.reconstruct(torch.zeros((1, 2, n, n), device="cuda"), 1,
+                         ext_out=torch.empty((1, 2, 256, 256), device="cuda"))
