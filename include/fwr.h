@@ -168,6 +168,39 @@ fwr_status fwr_reconstruct_host(fwr_plan* plan, const float* slopes_host, int n_
 fwr_status fwr_plan_reserve(fwr_plan* plan, int n_frames);
 
 /*
+ * fwr_reconstruct without any device allocation, for 256x256 grids.
+ * (The paper has no counterpart: this is a deployment convenience.)
+ *
+ * For callers that must not allocate GPU memory once they are running: a
+ * real-time control loop that forbids allocation after start-up (an
+ * allocation can stall for milliseconds), or a process whose device memory
+ * belongs to another allocator or to a fixed budget. Reconstructing a
+ * 256x256 grid needs 512 KB of working memory per frame in flight, which
+ * fwr_reconstruct takes from the plan (one area per SM, allocated when the
+ * plan is created). This entry point instead uses an array that is part of
+ * the library itself: room for FWR_STATIC_SCRATCH_GRIDS frames in flight
+ * (8 MB), present on every GPU that loads the library until the process
+ * exits. It calls no cudaMalloc or cudaFree.
+ *
+ *   plan          a plan with N = 256 (FWR_ERR_UNSUPPORTED otherwise)
+ *   slopes_dev, n_frames, iters, phase_dev, stream   as for fwr_reconstruct
+ *   ctas          frames processed concurrently, 1 .. FWR_STATIC_SCRATCH_GRIDS
+ *                 (FWR_ERR_ARG otherwise; fwr_last_error() says why); any
+ *                 n_frames is accepted, the CTAs loop over the frames
+ *
+ * The results equal fwr_reconstruct's. The array is shared by all calls on a
+ * device and keeps the last call's contents; nothing in it needs to start at
+ * zero, because every frame writes its whole area before reading it. Calls
+ * that overlap on the GPU (other streams, other threads, other plans) race on
+ * the array: serialise them. The first call on each device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.
+ */
+#define FWR_STATIC_SCRATCH_GRIDS 16
+fwr_status fwr_reconstruct_static(fwr_plan* plan, const float* slopes_dev, int n_frames, int iters,
+                                  float* phase_dev, int ctas, void* stream);
+
+/*
  * Batched 2-D FFT of n_frames complex N x N grids with the kernels' own
  * shared-memory FFT (the transform used inside the loop), FP32 interleaved
  * complex (re, im). Forward: X[ky][kx] = sum x[m][c] e^{-2 i pi (ky m + kx c)/N};

@@ -336,6 +336,42 @@ fwr_status fwr_reconstruct(fwr_plan* p, const float* slopes, int n_frames, int i
     return fwr_reconstruct_ex(p, slopes, nullptr, n_frames, iters, phase, nullptr, stream);
 }
 
+static_assert(FWR_STATIC_SCRATCH_GRIDS == fwr::STATIC_SLAB_GRIDS, "static scratch size mismatch");
+
+fwr_status fwr_reconstruct_static(fwr_plan* p, const float* slopes, int n_frames, int iters, float* phase, int ctas,
+                                  void* stream) {
+    fwr_status st = check_call(p, slopes, n_frames, iters, phase, nullptr);
+    if (st != FWR_OK) return st;
+    if (!phase && n_frames > 0) return FWR_ERR_ARG;
+    if (p->N != 256) {
+        std::snprintf(g_last_error, sizeof(g_last_error),
+                      "fwr_reconstruct_static: only 256x256 grids use scratch memory (plan grid is %d)", p->N);
+        return FWR_ERR_UNSUPPORTED;
+    }
+    if (ctas < 1 || ctas > FWR_STATIC_SCRATCH_GRIDS) {
+        std::snprintf(g_last_error, sizeof(g_last_error),
+                      "fwr_reconstruct_static: ctas = %d, the static scratch holds 1..%d grids of 256x256", ctas,
+                      FWR_STATIC_SCRATCH_GRIDS);
+        return FWR_ERR_ARG;
+    }
+    if (n_frames == 0) return FWR_OK;
+    fwr::Params<float> k;
+    k.tab = view(p->f32);
+    k.mask = p->d_mask;
+    k.slopes = slopes;
+    k.ext_init = nullptr;
+    k.phase = phase;
+    k.ext_out = nullptr;
+    k.n = p->n;
+    k.off = p->off;
+    k.F = n_frames;
+    k.iters = iters;
+    k.periodic = p->periodic;
+    k.status = p->d_status;
+    cudaError_t e = fwr::launch_slab_static(k, ctas, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? FWR_OK : cuda_fail(e, "static-scratch launch");
+}
+
 fwr_status fwr_reconstruct_f64(fwr_plan* p, const double* slopes, const double* ext_init, int n_frames, int iters,
                                double* phase, double* ext_out, void* stream) {
     fwr_status st = check_call(p, slopes, n_frames, iters, phase, ext_out);

@@ -54,6 +54,11 @@ size_t slab_smem_bytes(int n);
 size_t slab_scratch_elems_per_cta();
 int slab_max_ctas();
 cudaError_t launch_slab(const Params<float>& p, float2* scratch, int max_ctas, cudaStream_t s);
+// The same kernel on the library's static scratch array (no allocation):
+// at most STATIC_SLAB_GRIDS CTAs; cudaErrorInvalidValue for ctas outside
+// 1..STATIC_SLAB_GRIDS.
+enum : int { STATIC_SLAB_GRIDS = 16 };
+cudaError_t launch_slab_static(const Params<float>& p, int ctas, cudaStream_t s);
 
 // Main fused kernel (fwr_fused.cu). fused_supported() says whether its
 // shared-memory layout fits grid N with n lenslets for the element size.

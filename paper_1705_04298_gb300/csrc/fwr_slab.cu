@@ -27,6 +27,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "fwr_internal.h"
 
 namespace fwr {
@@ -292,6 +294,42 @@ cudaError_t launch_slab(const Params<float>& p, float2* scratch, int max_ctas, c
     if (e != cudaSuccess) return e;
     int grid = max_ctas < p.F ? max_ctas : p.F;
     if (grid < 1) return cudaErrorInvalidConfiguration;
+    slab_kernel<<<grid, SNT, smem, s>>>(p, scratch);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Variant without any allocation: the scratch is this file-scope array, sized
+// for STATIC_SLAB_GRIDS concurrent frames (8 MB). It exists on every GPU that
+// loads the library, for the life of the process.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) float2 g_static_slab_scratch[STATIC_SLAB_GRIDS * SN * SN];
+
+cudaError_t launch_slab_static(const Params<float>& p, int ctas, cudaStream_t s) {
+    if (ctas < 1 || ctas > STATIC_SLAB_GRIDS) return cudaErrorInvalidValue;
+    // Host code cannot use the array's name as a device address: look the
+    // address up once per device, with that device current, and cache it.
+    static std::mutex mu;
+    static float2* addr[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    float2* scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (!addr[dev]) {
+            void* ptr = nullptr;
+            e = cudaGetSymbolAddress(&ptr, g_static_slab_scratch);
+            if (e != cudaSuccess) return e;
+            addr[dev] = static_cast<float2*>(ptr);
+        }
+        scratch = addr[dev];
+    }
+    const size_t smem = slab_smem_bytes(p.n);
+    e = cudaFuncSetAttribute(slab_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    const int grid = ctas < p.F ? ctas : p.F;
     slab_kernel<<<grid, SNT, smem, s>>>(p, scratch);
     return cudaGetLastError();
 }

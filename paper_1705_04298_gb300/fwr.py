@@ -21,6 +21,7 @@ PERIODIC_BEFORE_EACH_FFT = 0
 PERIODIC_FINAL_ONLY = 1
 PERIODIC_NONE = 2
 OPT_PERIODIC = 1
+STATIC_SCRATCH_GRIDS = 16
 
 STATUS = {0: "FWR_OK", 1: "FWR_ERR_ARG", 2: "FWR_ERR_UNSUPPORTED", 3: "FWR_ERR_CUDA",
           4: "FWR_ERR_NONFINITE", 5: "FWR_ERR_TIMEOUT"}
@@ -39,6 +40,7 @@ SIGNATURES = {
     "fwr_reconstruct_ex": (_I, [_P, _P, _P, _I, _I, _P, _P, _P]),
     "fwr_reconstruct_f64": (_I, [_P, _P, _P, _I, _I, _P, _P, _P]),
     "fwr_reconstruct_host": (_I, [_P, _P, _I, _I, _P, _P]),
+    "fwr_reconstruct_static": (_I, [_P, _P, _I, _I, _P, _I, _P]),
     "fwr_plan_reserve": (_I, [_P, _I]),
     "fwr_fft2": (_I, [_I, _P, _P, _I, _I, _P]),
     "fwr_get_status": (_I, [_P]),
@@ -170,6 +172,21 @@ class Plan:
         _check(self._lib.fwr_reconstruct_f64(self._h, _ptr(slopes), _ptr(ext_init), F, int(iters),
                                              _ptr(phase), _ptr(ext_out), _stream(stream)),
                "fwr_reconstruct_f64")
+        return phase
+
+    def reconstruct_static(self, slopes, iters, phase=None, ctas=STATIC_SCRATCH_GRIDS, stream=None):
+        """256x256 grids without any device allocation (fwr_reconstruct_static):
+        the working memory is the library's own static array, shared by every
+        call on the device, so calls must not overlap on the GPU."""
+        import torch
+        F = slopes.shape[0]
+        n, N = self.n, self.N
+        _need(slopes, torch.float32, (F, 2, n, n), "slopes")
+        if phase is None:
+            phase = torch.empty((F, N, N), dtype=torch.float32, device=slopes.device)
+        _need(phase, torch.float32, (F, N, N), "phase")
+        _check(self._lib.fwr_reconstruct_static(self._h, _ptr(slopes), F, int(iters), _ptr(phase), int(ctas),
+                                                _stream(stream)), "fwr_reconstruct_static")
         return phase
 
     def reserve(self, n_frames):
