@@ -168,6 +168,55 @@ fwr_status fwr_reconstruct_host(fwr_plan* plan, const float* slopes_host, int n_
 fwr_status fwr_plan_reserve(fwr_plan* plan, int n_frames);
 
 /*
+ * Ragged batches: frames of several plans (128x128 and 256x256 grids mixed,
+ * e.g. pupils of 40, 64, 80 and 128 lenslets across) reconstructed by ONE
+ * persistent kernel launch. The batch fixes which plan each frame uses and
+ * the number of iterations; it owns a schedule (the frames each CTA
+ * processes, balanced on the host by longest-processing-time-first with a
+ * per-frame cost of 1 for 128x128 and `cost_ratio` for 256x256) and, when a
+ * 256x256 plan is present, the working memory of its frames (512 KB per SM).
+ *
+ * fwr_batch_create
+ *   plans        HOST array of n_plans plans on one device; each must have
+ *                N = 128 (n <= 85) or N = 256 (FWR_ERR_UNSUPPORTED otherwise).
+ *                The plans must outlive the batch; their options are read at
+ *                creation.
+ *   frame_plan   HOST array of n_frames plan indices, copied
+ *   iters        Gerchberg iterations for every frame (0..64)
+ * fwr_batch_run: one launch on `stream`, no allocation, no host
+ * synchronisation (CUDA-graph capturable).
+ *   slopes_dev   DEVICE array of n_frames device pointers; frame f points to
+ *                [2][n][n] floats of its plan
+ *   phase_dev    DEVICE array of n_frames device pointers to [N][N] floats
+ * Runs on one batch must not overlap on the GPU (shared working memory).
+ * fwr_batch_schedule re-balances with `ctas` persistent CTAs (1 .. SM count)
+ * and a 256x256/128x128 cost ratio; fwr_batch_autotune times candidate
+ * (ctas, cost_ratio) pairs on the caller's data (synchronises `stream`),
+ * keeps the fastest and appends it to the JSON-lines file cache_path (NULL:
+ * no cache); a cached entry for the same device, plans, frame counts and
+ * iterations is applied without timing.
+ */
+typedef struct fwr_batch fwr_batch;
+fwr_status fwr_batch_create(fwr_batch** out, fwr_plan* const* plans, int n_plans, const int* frame_plan,
+                            int n_frames, int iters);
+fwr_status fwr_batch_run(fwr_batch* batch, const float* const* slopes_dev, float* const* phase_dev,
+                         void* stream);
+fwr_status fwr_batch_schedule(fwr_batch* batch, int ctas, double cost_ratio);
+fwr_status fwr_batch_autotune(fwr_batch* batch, const float* const* slopes_dev, float* const* phase_dev,
+                              void* stream, const char* cache_path);
+int fwr_batch_ctas(const fwr_batch* batch);
+double fwr_batch_cost_ratio(const fwr_batch* batch);
+void fwr_batch_destroy(fwr_batch* batch);
+
+/*
+ * The schedule of ragged batches, on the host only: assign n jobs with
+ * costs[i] >= 0 to `ctas` workers, longest first to the least loaded worker.
+ * Output: worker c runs order[cta_off[c] .. cta_off[c+1]) (cta_off has
+ * ctas + 1 entries, order has n).
+ */
+fwr_status fwr_schedule_lpt(const double* costs, int n, int ctas, int* cta_off, int* order);
+
+/*
  * fwr_reconstruct without any device allocation, for 256x256 grids.
  * (The paper has no counterpart: this is a deployment convenience.)
  *

@@ -15,58 +15,38 @@
 
 #include "../../include/fwr.h"
 #include "fwr_internal.h"
+#include "fwr_plan.h"
 
 namespace {
 
 thread_local char g_last_error[256] = "";
 
-fwr_status cuda_fail(cudaError_t e, const char* where) {
+}  // namespace
+
+fwr_status fwr::cuda_fail(cudaError_t e, const char* where) {
     std::snprintf(g_last_error, sizeof(g_last_error), "%s: %s", where, cudaGetErrorString(e));
     return FWR_ERR_CUDA;
 }
 
+void fwr::set_last_error(const char* msg) { std::snprintf(g_last_error, sizeof(g_last_error), "%s", msg); }
+
+namespace {
+using fwr::cuda_fail;
+
 const double kPi = 3.14159265358979323846;
 const double kNullThreshold = 1e-14;
 
-// Device copies of one precision's tables.
-template <typename T> struct DevTables {
-    typedef typename fwr::cvec<T>::type V;
-    V* tw = nullptr;
-    V* A = nullptr;
-    V* Tt = nullptr;
-    T* pt = nullptr;
-    T* iota = nullptr;
-    T* wfin = nullptr;
-};
-
-template <typename T> void free_tables(DevTables<T>& t) {
+template <typename T> void free_tables(fwr::DevTables<T>& t) {
     cudaFree(t.tw);
     cudaFree(t.A);
     cudaFree(t.Tt);
     cudaFree(t.pt);
     cudaFree(t.iota);
     cudaFree(t.wfin);
-    t = DevTables<T>();
+    t = fwr::DevTables<T>();
 }
 
 }  // namespace
-
-struct fwr_plan {
-    int n = 0, N = 0, off = 0, filter = 0, periodic = FWR_PERIODIC_BEFORE_EACH_FFT, nvalid = 0;
-    int device = 0;
-    double noise_var = 0, r0 = 0, L0 = 0;
-    uint8_t* d_mask = nullptr;
-    unsigned* d_status = nullptr;
-    DevTables<float> f32;
-    DevTables<double> f64;
-    // 256^2 grids: per-CTA global scratch of the slab kernel
-    float2* d_scratch = nullptr;
-    int scratch_ctas = 0;
-    // host-path staging
-    float* d_stage_in = nullptr;
-    float* d_stage_out = nullptr;
-    int stage_frames = 0;
-};
 
 namespace {
 
@@ -149,7 +129,7 @@ HostTables build_tables(int N, int filter, double noise_var, double r0, double L
 }
 
 template <typename T>
-fwr_status upload_tables(const HostTables& h, int N, DevTables<T>& d) {
+fwr_status upload_tables(const HostTables& h, int N, fwr::DevTables<T>& d) {
     typedef typename fwr::cvec<T>::type V;
     const int H = N / 2;
     std::vector<T> tw(2 * N), A(2 * N), Tt(2 * N), pt(4 * size_t(N)), iota(size_t(H + 1) * N),
@@ -182,7 +162,7 @@ fwr_status upload_tables(const HostTables& h, int N, DevTables<T>& d) {
 }
 
 template <typename T>
-fwr::Tables<T> view(const DevTables<T>& d) {
+fwr::Tables<T> view(const fwr::DevTables<T>& d) {
     fwr::Tables<T> t;
     t.tw = d.tw;
     t.A = d.A;

@@ -1,39 +1,5 @@
-// Main fused persistent Gerchberg kernel for sm_103a.
-//
-// One CTA (4N threads) owns one frame at a time and keeps its N x N packed
-// grid Z = sx + i sy in shared memory for every iteration of Algorithm 1
-// (Sec. 3.3) and for the final reconstruction (Eqs. 2-3). HBM is read for the
-// measured slopes and written for the phase only.
-//
-// 2-D FFT in three register passes (N = 4R):
-//   P1  rows, R-point DFT over n1 of elements 4 n1 + n2, twiddle w_N^(n2 k1)
-//   P2  rows 4-point DFT over n2  x  columns 4-point DFT over m1 of rows
-//       R m1 + m2, column twiddle w_N^(m2 q1)
-//   P3  columns, R-point DFT over m2
-// Each pass writes back to the cells it read, so the spectrum ends in a
-// digit-permuted layout: bin (ky, kx) sits at row R (ky mod 4) + ky / 4 and
-// column 4 (kx mod R) + kx / R. The inverse transform runs the passes in
-// reverse with conjugate twiddles, ending back in natural order.
-//
-// Shared-memory layout: cell (row, col) at row * (N + 2) + col; every pass
-// addresses its cells as one base register plus compile-time offsets. The row
-// stride is 2 mod 16 (in 8-byte cells) and 16-byte aligned, so
-//   * the row stage (half-warp = 8 consecutive rows x 2 adjacent columns),
-//   * P2 (8 consecutive rows per quarter-warp, 16-byte accesses),
-//   * the column stage (32 consecutive columns of one row)
-// are all bank-conflict free.
-//
-// Fusions:
-//   * spectral step (Algorithm 1 step 2) sits between the forward and inverse
-//     P3: each thread keeps its own bins in registers and reads the partner
-//     bins (-k) of the other thread from shared memory;
-//   * reinsertion (step 4) and the x part of the periodic fill (Eq. PC) sit
-//     between the inverse and the next forward P1 (each row's sum comes from
-//     the 4 threads that hold it, through a small shared partial-sum array);
-//   * the y part of Eq. PC is applied in the frequency domain: setting the
-//     last row of y slopes to minus the column sums adds
-//     -Sy(0, kx) e^{2 i pi ky / N} to Sy(ky, kx), a rank-1 correction built
-//     from the ky = 0 row of the spectrum.
+// Main fused persistent Gerchberg kernel for sm_103a: kernels and launchers.
+// The device code (layout, passes, per-frame path) is in fwr_fused.cuh.
 
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -43,378 +9,28 @@
 namespace fwr {
 
 #include "fwr_fft.cuh"
-
-namespace {
-
-// s0 staging row stride (elements): n rounded up to 2 mod 16, like the grid,
-// so the row stage's reinsertion reads are bank-conflict free.
-__host__ __device__ __forceinline__ int s0_stride(int n) { return n + ((18 - (n & 15)) & 15); }
-
-// Row-stage role of a thread: row r, columns 4 n1 + n2. Each warp takes 16
-// consecutive rows and 2 adjacent n2.
-template <int N>
-__device__ __forceinline__ void row_role(int tid, int& r, int& n2) {
-    r = (tid >> 1) % N;
-    n2 = (tid & 1) + 2 * ((tid >> 1) / N);
-}
-
-template <typename T, int N>
-struct Layout {
-    typedef typename cvec<T>::type V;
-    static constexpr int R = N / 4, H = N / 2, S = N + 2;
-    static constexpr size_t z = 0;
-    static constexpr size_t xpart = z + size_t(N) * S * sizeof(V);
-    static constexpr size_t tw = xpart + size_t(4 * N) * sizeof(T);
-    static constexpr size_t tw1 = tw + size_t(N) * sizeof(V);
-    static constexpr size_t tw2 = tw1 + size_t(4 * R) * sizeof(V);
-    static constexpr size_t a = tw2 + size_t(3 * R) * sizeof(V);
-    static constexpr size_t t = a + size_t(N) * sizeof(V);
-    static constexpr size_t pt = t + size_t(N) * sizeof(V);
-    static constexpr size_t iota = pt + size_t(4 * N) * sizeof(T);
-    static constexpr size_t s0 = (iota + size_t(H + 1) * N * sizeof(T) + 15) & ~size_t(15);
-    static size_t bytes(int n) { return s0 + size_t(n) * s0_stride(n) * sizeof(V); }
-};
-
-__device__ __forceinline__ void store4(float* d, float a, float b, float c, float e) {
-    *reinterpret_cast<float4*>(d) = make_float4(a, b, c, e);
-}
-__device__ __forceinline__ void store4(double* d, double a, double b, double c, double e) {
-    reinterpret_cast<double2*>(d)[0] = make_double2(a, b);
-    reinterpret_cast<double2*>(d)[1] = make_double2(c, e);
-}
-
-// four adjacent cells (16-byte aligned) in and out
-__device__ __forceinline__ void load4(const float2* p, float2* x) {
-    const float4 a = reinterpret_cast<const float4*>(p)[0], b = reinterpret_cast<const float4*>(p)[1];
-    x[0] = make_float2(a.x, a.y);
-    x[1] = make_float2(a.z, a.w);
-    x[2] = make_float2(b.x, b.y);
-    x[3] = make_float2(b.z, b.w);
-}
-__device__ __forceinline__ void load4(const double2* p, double2* x) {
-#pragma unroll
-    for (int b = 0; b < 4; ++b) x[b] = p[b];
-}
-__device__ __forceinline__ void store4c(float2* p, const float2* x) {
-    reinterpret_cast<float4*>(p)[0] = make_float4(x[0].x, x[0].y, x[1].x, x[1].y);
-    reinterpret_cast<float4*>(p)[1] = make_float4(x[2].x, x[2].y, x[3].x, x[3].y);
-}
-__device__ __forceinline__ void store4c(double2* p, const double2* x) {
-#pragma unroll
-    for (int b = 0; b < 4; ++b) p[b] = x[b];
-}
-// the four separable factors of one frequency (16-byte aligned)
-__device__ __forceinline__ float4 load_pt(const float* p) { return *reinterpret_cast<const float4*>(p); }
-__device__ __forceinline__ double4 load_pt(const double* p) { return make_double4(p[0], p[1], p[2], p[3]); }
-
-template <bool INV, typename V>
-__device__ __forceinline__ V twiddle(V x, V w) {
-    return INV ? cmulc(w, x) : cmul(x, w);
-}
-
-// P2 in either direction over all R*R tasks (row radix-4 x column radix-4).
-// Task (m2, k1) owns rows R a + m2 and columns 4 k1 + b, a, b = 0..3.
-template <bool INV, int N, typename V>
-__device__ __forceinline__ void pass2(V* Z, const V* tw2) {
-    constexpr int R = N / 4, S = N + 2, NT = 4 * N, TASKS = R * R, PER = (TASKS + NT - 1) / NT;
-#pragma unroll
-    for (int i = 0; i < PER; ++i) {
-        const int t = threadIdx.x + i * NT;
-        if (TASKS % NT != 0 && t >= TASKS) break;
-        const int m2 = t % R, k1 = t / R;
-        V* base = Z + m2 * S + 4 * k1;
-        V x[4][4];
-#pragma unroll
-        for (int a = 0; a < 4; ++a) load4(base + R * S * a, x[a]);
-        if (!INV) {
-            // rows: 4-point DFT over n2 (second index)
-#pragma unroll
-            for (int a = 0; a < 4; ++a) dft_reg<4, false>(x[a]);
-            // columns: 4-point DFT over m1 (first index), then w_N^(m2 q1)
-#pragma unroll
-            for (int b = 0; b < 4; ++b) {
-                V c[4] = {x[0][b], x[1][b], x[2][b], x[3][b]};
-                dft_reg<4, false>(c);
-#pragma unroll
-                for (int a = 0; a < 4; ++a) x[a][b] = c[a];
-            }
-#pragma unroll
-            for (int a = 1; a < 4; ++a) {
-                const V w = tw2[(a - 1) * R + m2];
-#pragma unroll
-                for (int b = 0; b < 4; ++b) x[a][b] = twiddle<false>(x[a][b], w);
-            }
-        } else {
-#pragma unroll
-            for (int a = 1; a < 4; ++a) {
-                const V w = tw2[(a - 1) * R + m2];
-#pragma unroll
-                for (int b = 0; b < 4; ++b) x[a][b] = twiddle<true>(x[a][b], w);
-            }
-#pragma unroll
-            for (int b = 0; b < 4; ++b) {
-                V c[4] = {x[0][b], x[1][b], x[2][b], x[3][b]};
-                dft_reg<4, true>(c);
-#pragma unroll
-                for (int a = 0; a < 4; ++a) x[a][b] = c[a];
-            }
-#pragma unroll
-            for (int a = 0; a < 4; ++a) dft_reg<4, true>(x[a]);
-        }
-#pragma unroll
-        for (int a = 0; a < 4; ++a) store4c(base + R * S * a, x[a]);
-    }
-}
-
-}  // namespace
+#include "fwr_fused.cuh"
 
 template <typename T, int N>
 __global__ void __launch_bounds__(4 * N)
 fused_kernel(Params<T> p) {
-    typedef typename cvec<T>::type V;
-    typedef Layout<T, N> L;
-    constexpr int R = N / 4, NT = 4 * N, H = N / 2, S = L::S;
     extern __shared__ __align__(16) unsigned char smem[];
-    V* Z = reinterpret_cast<V*>(smem + L::z);
-    T* xpart = reinterpret_cast<T*>(smem + L::xpart);
-    V* tw = reinterpret_cast<V*>(smem + L::tw);
-    V* tw1 = reinterpret_cast<V*>(smem + L::tw1);
-    V* tw2 = reinterpret_cast<V*>(smem + L::tw2);
-    V* A = reinterpret_cast<V*>(smem + L::a);
-    V* Tt = reinterpret_cast<V*>(smem + L::t);
-    T* pt = reinterpret_cast<T*>(smem + L::pt);
-    T* iota = reinterpret_cast<T*>(smem + L::iota);
-    V* s0 = reinterpret_cast<V*>(smem + L::s0);
     __shared__ int s_bad;
-
-    const int tid = threadIdx.x;
-    const int n = p.n, off = p.off, nn = n * n, ns = s0_stride(n);
-
-    for (int i = tid; i < N; i += NT) {
-        tw[i] = p.tab.tw[i];
-        A[i] = p.tab.A[i];
-        Tt[i] = p.tab.Tt[i];
-    }
-    for (int i = tid; i < 4 * N; i += NT) pt[i] = p.tab.pt[i];
-    // 1/|G|^2 weights in storage-column order (entry [ky][col] holds kx(col)),
-    // so the lanes of a warp read consecutive words
-    for (int i = tid; i < (H + 1) * N; i += NT) {
-        const int col = i % N;
-        iota[i] = p.tab.iota[(i / N) * N + (col >> 2) + R * (col & 3)];
-    }
-    if (tid == 0) s_bad = 0;
-    __syncthreads();
-    for (int i = tid; i < 4 * R; i += NT) tw1[i] = tw[(i & 3) * (i >> 2)];
-    for (int i = tid; i < 3 * R; i += NT) tw2[i] = tw[(i % R) * (1 + i / R)];
-
-    // Row stage: row r, columns 4 n1 + n2 (row_role). Column stage: storage
-    // column gam = tid mod N, row block q1 = tid / N.
-    int r, n2;
-    row_role<N>(tid, r, n2);
-    const int gam = tid % N, q1 = tid / N;
-    V* const rowp = Z + r * S + n2;         // row-stage cells: rowp[4 k1]
-    V* const colp = Z + R * q1 * S + gam;   // column-stage cells: colp[S m2]
-    unsigned pmask = 0;
-    {
-        const int i = r - off;
-        if (i >= 0 && i < n) {
-#pragma unroll
-            for (int n1 = 0; n1 < R; ++n1) {
-                const int j = 4 * n1 + n2 - off;
-                if (j >= 0 && j < n && p.mask[i * n + j]) pmask |= 1u << n1;
-            }
-        }
-    }
-    const V* s0row = s0 + (r - off) * ns + (n2 - off);  // dereferenced only under pmask
-    // spectral roles: kx of the storage column and its partner -kx
-    const int kx = (gam >> 2) + R * (gam & 3);
-    const int kxn = (N - kx) & (N - 1);
-    const int gamp = 4 * (kxn % R) + kxn / R;
-    const int q1n = (4 - q1) & 3;
-    const V* const partp = Z + R * q1n * S + gamp;  // partner cells: partp[S q2']
-    const V Ax = A[kx], Tx = Tt[kx];
-    // separable factors of the LSQ projection: with P = Gx conj(Gy) = p(u) conj(p(v)),
-    // the projected bin is alpha z(k) + beta conj z(-k), alpha = iota (|G|^2/2 + Im P),
-    // beta = iota ((|Gx|^2 - |Gy|^2)/2 + i Re P)
-    const T pux = pt[4 * kx], puy = pt[4 * kx + 1], a2u = pt[4 * kx + 2], t2u = pt[4 * kx + 3];
-    const T* const ptv = pt + 4 * q1;              // ptv[16 q2 + c] = pt[4 ky + c]
-    const V* const twv = tw + q1;                  // twv[4 q2] = tw[ky]
-    const T* const iop = iota + q1 * N + gam;       // iop[4 N q2] = 1/|G|^2 at (ky, kx)
-    const T* const ion = iota + (N - q1) * N + gamp; // ion[-4 N q2] = 1/|G|^2 at (-ky, -kx)
-    const T* const wfp = p.tab.wfin + q1 * N + kx;
-    const T* const wfn = p.tab.wfin + (N - q1) * N + kxn;
-    const T half = T(0.5);
-    __syncthreads();
-
-    const int mode = p.periodic;
+    if (threadIdx.x == 0) s_bad = 0;
+    FusedCtx<T, N> c;
+    fused_setup<T, N>(c, smem, p.tab, p.mask, p.n, p.off, p.periodic);
+    const int nn = p.n * p.n;
     bool finite = true;
     for (int f = blockIdx.x; f < p.F; f += gridDim.x) {
-        const T* sl = p.slopes + size_t(f) * 2 * nn;
-        for (int c = tid; c < nn; c += NT) {
-            if (p.mask[c]) {
-                const int i = c / n, j = c - i * n;
-                const T vx = sl[c], vy = sl[nn + c];
-                finite &= isfinite(vx) && isfinite(vy);
-                s0[i * ns + j] = mk(vx, vy);
-            }
-        }
-        __syncthreads();
-
-        // embed: measurement in the pupil, warm start (or zero) outside
-        V x[R];
-        const T* ext = p.ext_init ? p.ext_init + size_t(f) * 2 * N * N : nullptr;
-#pragma unroll
-        for (int n1 = 0; n1 < R; ++n1) {
-            if (pmask & (1u << n1)) {
-                x[n1] = s0row[4 * n1];
-            } else if (ext) {
-                const int c = r * N + 4 * n1 + n2;
-                x[n1] = mk(ext[c], ext[N * N + c]);
-            } else {
-                x[n1] = mk(T(0), T(0));
-            }
-        }
-
-        for (int it = 0; it <= p.iters; ++it) {
-            const bool final = it == p.iters;
-            // Eq. PC before this forward FFT?
-            const bool fill = mode == PERIODIC_BEFORE_EACH_FFT || (mode == PERIODIC_FINAL_ONLY && final);
-            if (fill) {
-                // x part: last column of x slopes = -(sum of the other N-1 of its row)
-                T s = T(0);
-#pragma unroll
-                for (int n1 = 0; n1 < R; ++n1)
-                    if (!(n1 == R - 1 && n2 == 3)) s += x[n1].x;
-                xpart[n2 * N + r] = s;
-                __syncthreads();
-                if (n2 == 3) x[R - 1].x = -(((xpart[r] + xpart[N + r]) + xpart[2 * N + r]) + xpart[3 * N + r]);
-            }
-            if (final && p.ext_out) {
-                // extended slopes out: finish the fill in direct space first
-#pragma unroll
-                for (int n1 = 0; n1 < R; ++n1) rowp[4 * n1] = x[n1];
-                __syncthreads();
-                if (fill) {
-                    for (int c = tid >> 5; c < N; c += NT / 32) {
-                        T s = T(0);
-                        for (int rr = tid & 31; rr < N - 1; rr += 32) s += Z[rr * S + c].y;
-                        s = warp_sum(s);
-                        if ((tid & 31) == 0) Z[(N - 1) * S + c].y = -s;
-                    }
-                    __syncthreads();
-                }
-                T* eo = p.ext_out + size_t(f) * 2 * N * N;
-                for (int c = tid; c < N * N; c += NT) {
-                    const V z = Z[(c / N) * S + c % N];
-                    eo[c] = z.x;
-                    eo[N * N + c] = z.y;
-                }
-#pragma unroll
-                for (int n1 = 0; n1 < R; ++n1) x[n1] = rowp[4 * n1];
-                __syncthreads();
-                if (!p.phase) break;
-            }
-
-            // ---- P1 forward: rows, R-point DFT over n1, twiddle w^(n2 k1)
-            dft_reg<R, false>(x);
-#pragma unroll
-            for (int k1 = 1; k1 < R; ++k1) x[k1] = twiddle<false>(x[k1], tw1[k1 * 4 + n2]);
-#pragma unroll
-            for (int k1 = 0; k1 < R; ++k1) rowp[4 * k1] = x[k1];
-            __syncthreads();
-            // ---- P2 forward
-            pass2<false, N>(Z, tw2);
-            __syncthreads();
-            // ---- P3 forward: columns, R-point DFT over m2; bins stay in registers
-#pragma unroll
-            for (int m2 = 0; m2 < R; ++m2) x[m2] = colp[S * m2];
-            dft_reg<R, false>(x);
-#pragma unroll
-            for (int q2 = 0; q2 < R; ++q2) colp[S * q2] = x[q2];
-            __syncthreads();
-
-            // ---- spectral step on bins ky = q1 + 4 q2, kx
-            V ey = mk(T(0), T(0));
-            if (fill) {
-                // Sy(0, kx) = (Z(0,kx) - conj Z(0,-kx)) / (2i)
-                const V z0 = Z[gam], z0p = Z[gamp];
-                ey = mk(half * (z0.y + z0p.y), half * (z0p.x - z0.x));
-            }
-#pragma unroll
-            for (int q2 = 0; q2 < R; ++q2) {
-                // partner row of -ky: R q1n + q2n
-                const V z2 = q1 == 0 ? partp[S * ((R - q2) & (R - 1))] : partp[S * (R - 1 - q2)];
-                V z1 = x[q2];
-                V z2c = mk(z2.x, -z2.y);
-                if (fill) {
-                    // c = i * Sy(0,kx) * e^{2 i pi ky / N}
-                    const V tk = twv[4 * q2];
-                    const V c0 = cmul(ey, mk(tk.x, -tk.y));
-                    const V cy = mk(-c0.y, c0.x);
-                    z1 = csub(z1, cy);
-                    z2c = cadd(z2c, cy);
-                }
-                const bool lo = 4 * q2 + q1 <= H;  // ky <= N/2: weight stored at (ky, kx)
-                if (!final) {
-                    // Algorithm 1 step 2: LSQ phase, slopes re-synthesised through G
-                    const T w = lo ? iop[4 * N * q2] : ion[-4 * N * q2];
-                    const auto pv = load_pt(ptv + 16 * q2);
-                    const T pvx = pv.x, pvy = pv.y, a2v = pv.z, t2v = pv.w;
-                    const T Px = pux * pvx + puy * pvy, Py = puy * pvx - pux * pvy;
-                    const T g2 = a2u * t2v + t2u * a2v, dg = a2u * t2v - t2u * a2v;
-                    const T al = w * (half * g2 + Py), bx = half * w * dg, by = w * Px;
-                    x[q2] = mk(al * z1.x + bx * z2c.x - by * z2c.y, al * z1.y + bx * z2c.y + by * z2c.x);
-                } else {
-                    // Eq. 2: phi = Rx Sx + Ry Sy with 2 Sx = z1 + conj z2, 2 Sy = (z1 - conj z2) / i
-                    const int ky = q1 + 4 * q2;
-                    const V sx = cadd(z1, z2c);
-                    const V dd = csub(z1, z2c);
-                    const V sy = mk(dd.y, -dd.x);
-                    const V gx = cmul(Ax, Tt[ky]);
-                    const V gy = cmul(Tx, A[ky]);
-                    const T w = half * (lo ? wfp[4 * N * q2] : wfn[-4 * N * q2]);
-                    const V ph = cadd(cmulc(gx, sx), cmulc(gy, sy));
-                    x[q2] = mk(ph.x * w, ph.y * w);
-                }
-            }
-            // ---- P3 inverse
-            dft_reg<R, true>(x);
-            __syncthreads();
-#pragma unroll
-            for (int m2 = 0; m2 < R; ++m2) colp[S * m2] = x[m2];
-            __syncthreads();
-            // ---- P2 inverse
-            pass2<true, N>(Z, tw2);
-            __syncthreads();
-            // ---- P1 inverse
-#pragma unroll
-            for (int k1 = 0; k1 < R; ++k1) x[k1] = rowp[4 * k1];
-#pragma unroll
-            for (int k1 = 1; k1 < R; ++k1) x[k1] = twiddle<true>(x[k1], tw1[k1 * 4 + n2]);
-            dft_reg<R, true>(x);
-
-            if (!final) {
-                // Algorithm 1 step 4: measured slopes back in the pupil
-#pragma unroll
-                for (int n1 = 0; n1 < R; ++n1)
-                    if (pmask & (1u << n1)) x[n1] = s0row[4 * n1];
-            } else {
-                // real phase out, through shared memory for coalesced stores
-#pragma unroll
-                for (int n1 = 0; n1 < R; ++n1) rowp[4 * n1].x = x[n1].x;
-                __syncthreads();
-                T* ph = p.phase + size_t(f) * N * N;
-                for (int c = tid; c < N * N / 4; c += NT) {
-                    const V* zr = Z + ((4 * c) / N) * S + (4 * c) % N;
-                    store4(ph + 4 * c, zr[0].x, zr[1].x, zr[2].x, zr[3].x);
-                }
-            }
-        }
+        finite &= fused_frame<T, N>(c, p.slopes + size_t(f) * 2 * nn,
+                                    p.ext_init ? p.ext_init + size_t(f) * 2 * N * N : nullptr,
+                                    p.phase ? p.phase + size_t(f) * N * N : nullptr,
+                                    p.ext_out ? p.ext_out + size_t(f) * 2 * N * N : nullptr, p.iters);
         __syncthreads();
     }
     if (!finite) atomicOr(&s_bad, 1);
     __syncthreads();
-    if (tid == 0 && s_bad) atomicOr(p.status, STATUS_NONFINITE);
+    if (threadIdx.x == 0 && s_bad) atomicOr(p.status, STATUS_NONFINITE);
 }
 
 // Standalone batched 2-D FFT through the same three passes (test entry):

@@ -1,0 +1,495 @@
+// Device code of the main fused Gerchberg kernel (fwr_fused.cu), shared with
+// the ragged-batch kernel (fwr_ragged.cu). Included inside namespace fwr after
+// fwr_fft.cuh.
+#pragma once
+
+// Main fused persistent Gerchberg kernel for sm_103a.
+//
+// One CTA (4N threads) owns one frame at a time and keeps its N x N packed
+// grid Z = sx + i sy in shared memory for every iteration of Algorithm 1
+// (Sec. 3.3) and for the final reconstruction (Eqs. 2-3). HBM is read for the
+// measured slopes and written for the phase only.
+//
+// 2-D FFT in three register passes (N = 4R):
+//   P1  rows, R-point DFT over n1 of elements 4 n1 + n2, twiddle w_N^(n2 k1)
+//   P2  rows 4-point DFT over n2  x  columns 4-point DFT over m1 of rows
+//       R m1 + m2, column twiddle w_N^(m2 q1)
+//   P3  columns, R-point DFT over m2
+// Each pass writes back to the cells it read, so the spectrum ends in a
+// digit-permuted layout: bin (ky, kx) sits at row R (ky mod 4) + ky / 4 and
+// column 4 (kx mod R) + kx / R. The inverse transform runs the passes in
+// reverse with conjugate twiddles, ending back in natural order.
+//
+// Shared-memory layout: cell (row, col) at row * (N + 2) + col; every pass
+// addresses its cells as one base register plus compile-time offsets. The row
+// stride is 2 mod 16 (in 8-byte cells) and 16-byte aligned, so
+//   * the row stage (half-warp = 8 consecutive rows x 2 adjacent columns),
+//   * P2 (8 consecutive rows per quarter-warp, 16-byte accesses),
+//   * the column stage (32 consecutive columns of one row)
+// are all bank-conflict free.
+//
+// Fusions:
+//   * spectral step (Algorithm 1 step 2) sits between the forward and inverse
+//     P3: each thread keeps its own bins in registers and reads the partner
+//     bins (-k) of the other thread from shared memory;
+//   * reinsertion (step 4) and the x part of the periodic fill (Eq. PC) sit
+//     between the inverse and the next forward P1 (each row's sum comes from
+//     the 4 threads that hold it, through a small shared partial-sum array);
+//   * the y part of Eq. PC is applied in the frequency domain: setting the
+//     last row of y slopes to minus the column sums adds
+//     -Sy(0, kx) e^{2 i pi ky / N} to Sy(ky, kx), a rank-1 correction built
+//     from the ky = 0 row of the spectrum.
+
+namespace {
+
+// s0 staging row stride (elements): n rounded up to 2 mod 16, like the grid,
+// so the row stage's reinsertion reads are bank-conflict free.
+__host__ __device__ __forceinline__ int s0_stride(int n) { return n + ((18 - (n & 15)) & 15); }
+
+// Row-stage role of a thread: row r, columns 4 n1 + n2. Each warp takes 16
+// consecutive rows and 2 adjacent n2.
+template <int N>
+__device__ __forceinline__ void row_role(int tid, int& r, int& n2) {
+    r = (tid >> 1) % N;
+    n2 = (tid & 1) + 2 * ((tid >> 1) / N);
+}
+
+template <typename T, int N>
+struct Layout {
+    typedef typename cvec<T>::type V;
+    static constexpr int R = N / 4, H = N / 2, S = N + 2;
+    static constexpr size_t z = 0;
+    static constexpr size_t xpart = z + size_t(N) * S * sizeof(V);
+    static constexpr size_t tw = xpart + size_t(4 * N) * sizeof(T);
+    static constexpr size_t tw1 = tw + size_t(N) * sizeof(V);
+    static constexpr size_t tw2 = tw1 + size_t(4 * R) * sizeof(V);
+    static constexpr size_t a = tw2 + size_t(3 * R) * sizeof(V);
+    static constexpr size_t t = a + size_t(N) * sizeof(V);
+    static constexpr size_t pt = t + size_t(N) * sizeof(V);
+    static constexpr size_t iota = pt + size_t(4 * N) * sizeof(T);
+    static constexpr size_t s0 = (iota + size_t(H + 1) * N * sizeof(T) + 15) & ~size_t(15);
+    static size_t bytes(int n) { return s0 + size_t(n) * s0_stride(n) * sizeof(V); }
+};
+
+__device__ __forceinline__ void store4(float* d, float a, float b, float c, float e) {
+    *reinterpret_cast<float4*>(d) = make_float4(a, b, c, e);
+}
+__device__ __forceinline__ void store4(double* d, double a, double b, double c, double e) {
+    reinterpret_cast<double2*>(d)[0] = make_double2(a, b);
+    reinterpret_cast<double2*>(d)[1] = make_double2(c, e);
+}
+
+// four adjacent cells (16-byte aligned) in and out
+__device__ __forceinline__ void load4(const float2* p, float2* x) {
+    const float4 a = reinterpret_cast<const float4*>(p)[0], b = reinterpret_cast<const float4*>(p)[1];
+    x[0] = make_float2(a.x, a.y);
+    x[1] = make_float2(a.z, a.w);
+    x[2] = make_float2(b.x, b.y);
+    x[3] = make_float2(b.z, b.w);
+}
+__device__ __forceinline__ void load4(const double2* p, double2* x) {
+#pragma unroll
+    for (int b = 0; b < 4; ++b) x[b] = p[b];
+}
+__device__ __forceinline__ void store4c(float2* p, const float2* x) {
+    reinterpret_cast<float4*>(p)[0] = make_float4(x[0].x, x[0].y, x[1].x, x[1].y);
+    reinterpret_cast<float4*>(p)[1] = make_float4(x[2].x, x[2].y, x[3].x, x[3].y);
+}
+__device__ __forceinline__ void store4c(double2* p, const double2* x) {
+#pragma unroll
+    for (int b = 0; b < 4; ++b) p[b] = x[b];
+}
+// the four separable factors of one frequency (16-byte aligned)
+template <typename T> struct quad { T x, y, z, w; };
+__device__ __forceinline__ quad<float> load_pt(const float* p) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    return {v.x, v.y, v.z, v.w};
+}
+__device__ __forceinline__ quad<double> load_pt(const double* p) { return {p[0], p[1], p[2], p[3]}; }
+
+template <bool INV, typename V>
+__device__ __forceinline__ V twiddle(V x, V w) {
+    return INV ? cmulc(w, x) : cmul(x, w);
+}
+
+// P2 in either direction over all R*R tasks (row radix-4 x column radix-4).
+// Task (m2, k1) owns rows R a + m2 and columns 4 k1 + b, a, b = 0..3.
+template <bool INV, int N, typename V>
+__device__ __forceinline__ void pass2(V* Z, const V* tw2) {
+    constexpr int R = N / 4, S = N + 2, NT = 4 * N, TASKS = R * R, PER = (TASKS + NT - 1) / NT;
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        const int t = threadIdx.x + i * NT;
+        if (TASKS % NT != 0 && t >= TASKS) break;
+        const int m2 = t % R, k1 = t / R;
+        V* base = Z + m2 * S + 4 * k1;
+        V x[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) load4(base + R * S * a, x[a]);
+        if (!INV) {
+            // rows: 4-point DFT over n2 (second index)
+#pragma unroll
+            for (int a = 0; a < 4; ++a) dft_reg<4, false>(x[a]);
+            // columns: 4-point DFT over m1 (first index), then w_N^(m2 q1)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                V c[4] = {x[0][b], x[1][b], x[2][b], x[3][b]};
+                dft_reg<4, false>(c);
+#pragma unroll
+                for (int a = 0; a < 4; ++a) x[a][b] = c[a];
+            }
+#pragma unroll
+            for (int a = 1; a < 4; ++a) {
+                const V w = tw2[(a - 1) * R + m2];
+#pragma unroll
+                for (int b = 0; b < 4; ++b) x[a][b] = twiddle<false>(x[a][b], w);
+            }
+        } else {
+#pragma unroll
+            for (int a = 1; a < 4; ++a) {
+                const V w = tw2[(a - 1) * R + m2];
+#pragma unroll
+                for (int b = 0; b < 4; ++b) x[a][b] = twiddle<true>(x[a][b], w);
+            }
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                V c[4] = {x[0][b], x[1][b], x[2][b], x[3][b]};
+                dft_reg<4, true>(c);
+#pragma unroll
+                for (int a = 0; a < 4; ++a) x[a][b] = c[a];
+            }
+#pragma unroll
+            for (int a = 0; a < 4; ++a) dft_reg<4, true>(x[a]);
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a) store4c(base + R * S * a, x[a]);
+    }
+}
+
+}  // namespace
+
+// Per-CTA state of the main kernel for one plan: shared-memory layout and
+// the per-thread roles and constants.
+template <typename T, int N>
+struct FusedCtx {
+    typedef typename cvec<T>::type V;
+    V* Z;
+    T* xpart;
+    V* tw;
+    V* tw1;
+    V* tw2;
+    V* A;
+    V* Tt;
+    T* pt;
+    T* iota;
+    V* s0;
+    const uint8_t* mask;
+    int n, off, nn, ns, mode;
+    int r, n2, gam, q1, kx, kxn, gamp;
+    V* rowp;
+    V* colp;
+    const V* partp;
+    const V* s0row;
+    unsigned pmask;
+    V Ax, Tx;
+    T pux, puy, a2u, t2u;
+    const T* ptv;
+    const V* twv;
+    const T* iop;
+    const T* ion;
+    const T* wfp;
+    const T* wfn;
+};
+
+// Load a plan's tables into shared memory and set the per-thread roles.
+// Called by every thread of the CTA; ends with a barrier.
+template <typename T, int N>
+__device__ __forceinline__ void fused_setup(FusedCtx<T, N>& c, unsigned char* smem, const Tables<T>& tab,
+                                            const uint8_t* mask, int n, int off, int mode) {
+    typedef typename cvec<T>::type V;
+    typedef Layout<T, N> L;
+    constexpr int R = N / 4, NT = 4 * N, H = N / 2, S = L::S;
+    V* Z = c.Z = reinterpret_cast<V*>(smem + L::z);
+    c.xpart = reinterpret_cast<T*>(smem + L::xpart);
+    V* tw = c.tw = reinterpret_cast<V*>(smem + L::tw);
+    V* tw1 = c.tw1 = reinterpret_cast<V*>(smem + L::tw1);
+    V* tw2 = c.tw2 = reinterpret_cast<V*>(smem + L::tw2);
+    V* A = c.A = reinterpret_cast<V*>(smem + L::a);
+    V* Tt = c.Tt = reinterpret_cast<V*>(smem + L::t);
+    T* pt = c.pt = reinterpret_cast<T*>(smem + L::pt);
+    T* iota = c.iota = reinterpret_cast<T*>(smem + L::iota);
+    V* s0 = c.s0 = reinterpret_cast<V*>(smem + L::s0);
+    c.mask = mask;
+    c.n = n;
+    c.off = off;
+    c.nn = n * n;
+    const int ns = c.ns = s0_stride(n);
+    c.mode = mode;
+    const int tid = threadIdx.x;
+
+    for (int i = tid; i < N; i += NT) {
+        tw[i] = tab.tw[i];
+        A[i] = tab.A[i];
+        Tt[i] = tab.Tt[i];
+    }
+    for (int i = tid; i < 4 * N; i += NT) pt[i] = tab.pt[i];
+    // 1/|G|^2 weights in storage-column order (entry [ky][col] holds kx(col)),
+    // so the lanes of a warp read consecutive words
+    for (int i = tid; i < (H + 1) * N; i += NT) {
+        const int col = i % N;
+        iota[i] = tab.iota[(i / N) * N + (col >> 2) + R * (col & 3)];
+    }
+    __syncthreads();
+    for (int i = tid; i < 4 * R; i += NT) tw1[i] = tw[(i & 3) * (i >> 2)];
+    for (int i = tid; i < 3 * R; i += NT) tw2[i] = tw[(i % R) * (1 + i / R)];
+
+    // Row stage: row r, columns 4 n1 + n2 (row_role). Column stage: storage
+    // column gam = tid mod N, row block q1 = tid / N.
+    int r, n2;
+    row_role<N>(tid, r, n2);
+    const int gam = tid % N, q1 = tid / N;
+    c.r = r;
+    c.n2 = n2;
+    c.gam = gam;
+    c.q1 = q1;
+    c.rowp = Z + r * S + n2;         // row-stage cells: rowp[4 k1]
+    c.colp = Z + R * q1 * S + gam;   // column-stage cells: colp[S m2]
+    unsigned pmask = 0;
+    {
+        const int i = r - off;
+        if (i >= 0 && i < n) {
+#pragma unroll
+            for (int n1 = 0; n1 < R; ++n1) {
+                const int j = 4 * n1 + n2 - off;
+                if (j >= 0 && j < n && mask[i * n + j]) pmask |= 1u << n1;
+            }
+        }
+    }
+    c.pmask = pmask;
+    c.s0row = s0 + (r - off) * ns + (n2 - off);  // dereferenced only under pmask
+    // spectral roles: kx of the storage column and its partner -kx
+    const int kx = (gam >> 2) + R * (gam & 3);
+    const int kxn = (N - kx) & (N - 1);
+    const int gamp = 4 * (kxn % R) + kxn / R;
+    const int q1n = (4 - q1) & 3;
+    c.kx = kx;
+    c.kxn = kxn;
+    c.gamp = gamp;
+    c.partp = Z + R * q1n * S + gamp;  // partner cells: partp[S q2']
+    c.Ax = A[kx];
+    c.Tx = Tt[kx];
+    // separable factors of the LSQ projection: with P = Gx conj(Gy) = p(u) conj(p(v)),
+    // the projected bin is alpha z(k) + beta conj z(-k), alpha = iota (|G|^2/2 + Im P),
+    // beta = iota ((|Gx|^2 - |Gy|^2)/2 + i Re P)
+    c.pux = pt[4 * kx];
+    c.puy = pt[4 * kx + 1];
+    c.a2u = pt[4 * kx + 2];
+    c.t2u = pt[4 * kx + 3];
+    c.ptv = pt + 4 * q1;              // ptv[16 q2 + j] = pt[4 ky + j]
+    c.twv = tw + q1;                  // twv[4 q2] = tw[ky]
+    c.iop = iota + q1 * N + gam;       // iop[4 N q2] = 1/|G|^2 at (ky, kx)
+    c.ion = iota + (N - q1) * N + gamp; // ion[-4 N q2] = 1/|G|^2 at (-ky, -kx)
+    c.wfp = tab.wfin + q1 * N + kx;
+    c.wfn = tab.wfin + (N - q1) * N + kxn;
+    __syncthreads();
+
+}
+
+// One frame through the whole path (embed, iterations, final filter) with
+// the state of fused_setup. sl: the frame's [2][n][n] slopes; ext: [2][N][N]
+// warm start or nullptr; phase: [N][N] output or nullptr; ext_out: [2][N][N]
+// extended slopes or nullptr. Called by every thread; returns false in the
+// threads that saw a non-finite measured slope.
+template <typename T, int N>
+__device__ __forceinline__ bool fused_frame(const FusedCtx<T, N>& c, const T* sl, const T* ext, T* phase,
+                                            T* ext_out, int iters) {
+    typedef typename cvec<T>::type V;
+    constexpr int R = N / 4, NT = 4 * N, H = N / 2, S = Layout<T, N>::S;
+    const int tid = threadIdx.x;
+    V* const Z = c.Z;
+    T* const xpart = c.xpart;
+    const V* const tw1 = c.tw1;
+    const V* const tw2 = c.tw2;
+    const V* const A = c.A;
+    const V* const Tt = c.Tt;
+    V* const s0 = c.s0;
+    const uint8_t* const mask = c.mask;
+    const int n = c.n, nn = c.nn, ns = c.ns, mode = c.mode;
+    const int r = c.r, n2 = c.n2, gam = c.gam, q1 = c.q1, kx = c.kx, kxn = c.kxn, gamp = c.gamp;
+    V* const rowp = c.rowp;
+    V* const colp = c.colp;
+    const V* const partp = c.partp;
+    const V* const s0row = c.s0row;
+    const unsigned pmask = c.pmask;
+    const V Ax = c.Ax, Tx = c.Tx;
+    const T pux = c.pux, puy = c.puy, a2u = c.a2u, t2u = c.t2u;
+    const T* const ptv = c.ptv;
+    const V* const twv = c.twv;
+    const T* const iop = c.iop;
+    const T* const ion = c.ion;
+    const T* const wfp = c.wfp;
+    const T* const wfn = c.wfn;
+    const T half = T(0.5);
+    bool finite = true;
+    for (int c = tid; c < nn; c += NT) {
+        if (mask[c]) {
+            const int i = c / n, j = c - i * n;
+            const T vx = sl[c], vy = sl[nn + c];
+            finite &= isfinite(vx) && isfinite(vy);
+            s0[i * ns + j] = mk(vx, vy);
+        }
+    }
+    __syncthreads();
+
+    // embed: measurement in the pupil, warm start (or zero) outside
+    V x[R];
+#pragma unroll
+    for (int n1 = 0; n1 < R; ++n1) {
+        if (pmask & (1u << n1)) {
+            x[n1] = s0row[4 * n1];
+        } else if (ext) {
+            const int c = r * N + 4 * n1 + n2;
+            x[n1] = mk(ext[c], ext[N * N + c]);
+        } else {
+            x[n1] = mk(T(0), T(0));
+        }
+    }
+
+    for (int it = 0; it <= iters; ++it) {
+        const bool final = it == iters;
+        // Eq. PC before this forward FFT?
+        const bool fill = mode == PERIODIC_BEFORE_EACH_FFT || (mode == PERIODIC_FINAL_ONLY && final);
+        if (fill) {
+            // x part: last column of x slopes = -(sum of the other N-1 of its row)
+            T s = T(0);
+#pragma unroll
+            for (int n1 = 0; n1 < R; ++n1)
+                if (!(n1 == R - 1 && n2 == 3)) s += x[n1].x;
+            xpart[n2 * N + r] = s;
+            __syncthreads();
+            if (n2 == 3) x[R - 1].x = -(((xpart[r] + xpart[N + r]) + xpart[2 * N + r]) + xpart[3 * N + r]);
+        }
+        if (final && ext_out) {
+            // extended slopes out: finish the fill in direct space first
+#pragma unroll
+            for (int n1 = 0; n1 < R; ++n1) rowp[4 * n1] = x[n1];
+            __syncthreads();
+            if (fill) {
+                for (int c = tid >> 5; c < N; c += NT / 32) {
+                    T s = T(0);
+                    for (int rr = tid & 31; rr < N - 1; rr += 32) s += Z[rr * S + c].y;
+                    s = warp_sum(s);
+                    if ((tid & 31) == 0) Z[(N - 1) * S + c].y = -s;
+                }
+                __syncthreads();
+            }
+            T* eo = ext_out;
+            for (int c = tid; c < N * N; c += NT) {
+                const V z = Z[(c / N) * S + c % N];
+                eo[c] = z.x;
+                eo[N * N + c] = z.y;
+            }
+#pragma unroll
+            for (int n1 = 0; n1 < R; ++n1) x[n1] = rowp[4 * n1];
+            __syncthreads();
+            if (!phase) break;
+        }
+
+        // ---- P1 forward: rows, R-point DFT over n1, twiddle w^(n2 k1)
+        dft_reg<R, false>(x);
+#pragma unroll
+        for (int k1 = 1; k1 < R; ++k1) x[k1] = twiddle<false>(x[k1], tw1[k1 * 4 + n2]);
+#pragma unroll
+        for (int k1 = 0; k1 < R; ++k1) rowp[4 * k1] = x[k1];
+        __syncthreads();
+        // ---- P2 forward
+        pass2<false, N>(Z, tw2);
+        __syncthreads();
+        // ---- P3 forward: columns, R-point DFT over m2; bins stay in registers
+#pragma unroll
+        for (int m2 = 0; m2 < R; ++m2) x[m2] = colp[S * m2];
+        dft_reg<R, false>(x);
+#pragma unroll
+        for (int q2 = 0; q2 < R; ++q2) colp[S * q2] = x[q2];
+        __syncthreads();
+
+        // ---- spectral step on bins ky = q1 + 4 q2, kx
+        V ey = mk(T(0), T(0));
+        if (fill) {
+            // Sy(0, kx) = (Z(0,kx) - conj Z(0,-kx)) / (2i)
+            const V z0 = Z[gam], z0p = Z[gamp];
+            ey = mk(half * (z0.y + z0p.y), half * (z0p.x - z0.x));
+        }
+#pragma unroll
+        for (int q2 = 0; q2 < R; ++q2) {
+            // partner row of -ky: R q1n + q2n
+            const V z2 = q1 == 0 ? partp[S * ((R - q2) & (R - 1))] : partp[S * (R - 1 - q2)];
+            V z1 = x[q2];
+            V z2c = mk(z2.x, -z2.y);
+            if (fill) {
+                // c = i * Sy(0,kx) * e^{2 i pi ky / N}
+                const V tk = twv[4 * q2];
+                const V c0 = cmul(ey, mk(tk.x, -tk.y));
+                const V cy = mk(-c0.y, c0.x);
+                z1 = csub(z1, cy);
+                z2c = cadd(z2c, cy);
+            }
+            const bool lo = 4 * q2 + q1 <= H;  // ky <= N/2: weight stored at (ky, kx)
+            if (!final) {
+                // Algorithm 1 step 2: LSQ phase, slopes re-synthesised through G
+                const T w = lo ? iop[4 * N * q2] : ion[-4 * N * q2];
+                const auto pv = load_pt(ptv + 16 * q2);
+                const T pvx = pv.x, pvy = pv.y, a2v = pv.z, t2v = pv.w;
+                const T Px = pux * pvx + puy * pvy, Py = puy * pvx - pux * pvy;
+                const T g2 = a2u * t2v + t2u * a2v, dg = a2u * t2v - t2u * a2v;
+                const T al = w * (half * g2 + Py), bx = half * w * dg, by = w * Px;
+                x[q2] = mk(al * z1.x + bx * z2c.x - by * z2c.y, al * z1.y + bx * z2c.y + by * z2c.x);
+            } else {
+                // Eq. 2: phi = Rx Sx + Ry Sy with 2 Sx = z1 + conj z2, 2 Sy = (z1 - conj z2) / i
+                const int ky = q1 + 4 * q2;
+                const V sx = cadd(z1, z2c);
+                const V dd = csub(z1, z2c);
+                const V sy = mk(dd.y, -dd.x);
+                const V gx = cmul(Ax, Tt[ky]);
+                const V gy = cmul(Tx, A[ky]);
+                const T w = half * (lo ? wfp[4 * N * q2] : wfn[-4 * N * q2]);
+                const V ph = cadd(cmulc(gx, sx), cmulc(gy, sy));
+                x[q2] = mk(ph.x * w, ph.y * w);
+            }
+        }
+        // ---- P3 inverse
+        dft_reg<R, true>(x);
+        __syncthreads();
+#pragma unroll
+        for (int m2 = 0; m2 < R; ++m2) colp[S * m2] = x[m2];
+        __syncthreads();
+        // ---- P2 inverse
+        pass2<true, N>(Z, tw2);
+        __syncthreads();
+        // ---- P1 inverse
+#pragma unroll
+        for (int k1 = 0; k1 < R; ++k1) x[k1] = rowp[4 * k1];
+#pragma unroll
+        for (int k1 = 1; k1 < R; ++k1) x[k1] = twiddle<true>(x[k1], tw1[k1 * 4 + n2]);
+        dft_reg<R, true>(x);
+
+        if (!final) {
+            // Algorithm 1 step 4: measured slopes back in the pupil
+#pragma unroll
+            for (int n1 = 0; n1 < R; ++n1)
+                if (pmask & (1u << n1)) x[n1] = s0row[4 * n1];
+        } else {
+            // real phase out, through shared memory for coalesced stores
+#pragma unroll
+            for (int n1 = 0; n1 < R; ++n1) rowp[4 * n1].x = x[n1].x;
+            __syncthreads();
+            T* ph = phase;
+            for (int c = tid; c < N * N / 4; c += NT) {
+                const V* zr = Z + ((4 * c) / N) * S + (4 * c) % N;
+                store4(ph + 4 * c, zr[0].x, zr[1].x, zr[2].x, zr[3].x);
+            }
+        }
+    }
+    return finite;
+}
+

@@ -60,6 +60,29 @@ cudaError_t launch_slab(const Params<float>& p, float2* scratch, int max_ctas, c
 enum : int { STATIC_SLAB_GRIDS = 16 };
 cudaError_t launch_slab_static(const Params<float>& p, int ctas, cudaStream_t s);
 
+// Ragged batches (fwr_ragged.cu): one launch over frames of several plans
+// with N in {128, 256}. cta_off[grid + 1] / order[] list each CTA's frames;
+// slopes[f] / phase[f] are the frame's device pointers.
+struct RaggedPlan {
+    Tables<float> tab;
+    const uint8_t* mask;
+    unsigned* status;
+    int N, n, off, periodic;
+};
+struct RaggedParams {
+    const RaggedPlan* plans;
+    const int* frame_plan;
+    const int* cta_off;
+    const int* order;
+    const float* const* slopes;
+    float* const* phase;
+    float2* scratch;  // grid x 256^2 (only when a 256^2 plan is present)
+    int iters;
+};
+size_t ragged_smem_bytes(int N, int n);  // 0 if the plan cannot join a ragged batch
+cudaError_t ragged_prepare(size_t smem);
+cudaError_t launch_ragged(const RaggedParams& p, int grid, size_t smem, cudaStream_t s);
+
 // Main fused kernel (fwr_fused.cu). fused_supported() says whether its
 // shared-memory layout fits grid N with n lenslets for the element size.
 bool fused_supported(int N, int elem_bytes, int n);

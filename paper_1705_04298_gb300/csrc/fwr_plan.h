@@ -1,0 +1,46 @@
+// Plan object shared by the C-ABI translation units (fwr_api.cpp,
+// fwr_batch.cpp). Not installed.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/fwr.h"
+#include "fwr_internal.h"
+
+namespace fwr {
+
+// Device copies of one precision's tables.
+template <typename T> struct DevTables {
+    typedef typename cvec<T>::type V;
+    V* tw = nullptr;
+    V* A = nullptr;
+    V* Tt = nullptr;
+    T* pt = nullptr;
+    T* iota = nullptr;
+    T* wfin = nullptr;
+};
+
+// Record a CUDA error as the thread's last error; returns FWR_ERR_CUDA.
+fwr_status cuda_fail(cudaError_t e, const char* where);
+// Record a message as the thread's last error.
+void set_last_error(const char* msg);
+
+}  // namespace fwr
+
+struct fwr_plan {
+    int n = 0, N = 0, off = 0, filter = 0, periodic = FWR_PERIODIC_BEFORE_EACH_FFT, nvalid = 0;
+    int device = 0;
+    double noise_var = 0, r0 = 0, L0 = 0;
+    uint8_t* d_mask = nullptr;
+    unsigned* d_status = nullptr;
+    fwr::DevTables<float> f32;
+    fwr::DevTables<double> f64;
+    // 256^2 grids: per-CTA global scratch of the slab kernel
+    float2* d_scratch = nullptr;
+    int scratch_ctas = 0;
+    // host-path staging
+    float* d_stage_in = nullptr;
+    float* d_stage_out = nullptr;
+    int stage_frames = 0;
+};

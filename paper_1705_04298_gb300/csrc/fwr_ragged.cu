@@ -1,0 +1,63 @@
+// Ragged batches (sm_103a): one persistent launch over frames of several
+// plans, 128^2 and 256^2 grids mixed. Each CTA walks its own list of frames
+// (built on the host by a longest-processing-time-first schedule, grouped by
+// plan); when the plan changes it reloads that plan's tables into shared
+// memory, then runs the frame through the main kernel's per-frame path
+// (128^2) or the slab path (256^2, with this CTA's scratch area). Both paths
+// run on 512 threads.
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fwr_internal.h"
+
+namespace fwr {
+
+#include "fwr_fft.cuh"
+#include "fwr_fused.cuh"
+#include "fwr_slab.cuh"
+
+static_assert(4 * 128 == SNT, "both paths of the ragged kernel run on 512 threads");
+
+__global__ void __launch_bounds__(512, 1)
+ragged_kernel(RaggedParams rp) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int b = blockIdx.x;
+    const int i0 = rp.cta_off[b], i1 = rp.cta_off[b + 1];
+    float2* G = rp.scratch ? rp.scratch + size_t(b) * SN * SN : nullptr;
+    FusedCtx<float, 128> fc;
+    SlabCtx sc;
+    int cur = -1;
+    for (int i = i0; i < i1; ++i) {
+        const int f = rp.order[i];
+        const int pl = rp.frame_plan[f];
+        const RaggedPlan P = rp.plans[pl];
+        if (pl != cur) {
+            if (P.N == 128) fused_setup<float, 128>(fc, smem, P.tab, P.mask, P.n, P.off, P.periodic);
+            else slab_setup(sc, smem, P.tab, P.mask, P.n, P.off, P.periodic);
+            cur = pl;
+        }
+        bool ok;
+        if (P.N == 128) ok = fused_frame<float, 128>(fc, rp.slopes[f], nullptr, rp.phase[f], nullptr, rp.iters);
+        else ok = slab_frame(sc, P.tab, rp.slopes[f], nullptr, rp.phase[f], rp.iters, G);
+        if (!ok) atomicOr(P.status, STATUS_NONFINITE);
+        __syncthreads();
+    }
+}
+
+size_t ragged_smem_bytes(int N, int n) {
+    if (N == 128) return Layout<float, 128>::bytes(n);
+    if (N == 256) return slab_layout_bytes(n);
+    return 0;
+}
+
+cudaError_t ragged_prepare(size_t smem) {
+    return cudaFuncSetAttribute(ragged_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+}
+
+cudaError_t launch_ragged(const RaggedParams& p, int grid, size_t smem, cudaStream_t s) {
+    ragged_kernel<<<grid, 512, smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace fwr

@@ -1,28 +1,5 @@
-// Gerchberg kernel for 256^2 grids (sm_103a): slab-streamed through shared memory.
-//
-// A 256 x 256 complex grid (512 KB) does not fit one SM's shared memory, so
-// each persistent CTA keeps its frame's packed grid Z = sx + i sy in its own
-// area of a global scratch buffer (L2 resident: 512 KB per CTA) and streams
-// it through shared memory in slabs of 64 lines:
-//
-//   row phase, 4 slabs of 64 rows:     inverse row FFTs, reinsertion of the
-//                                      measured slopes (Algorithm 1 step 4),
-//                                      x part of the periodic fill (Eq. PC),
-//                                      forward row FFTs
-//   column phase, 4 slabs of 64 cols:  forward column FFTs, y part of Eq. PC
-//                                      as a spectral correction, the LSQ
-//                                      projection (Sec. 3.3) or the final
-//                                      filter (Eqs. 2-3), inverse column FFTs
-//
-// Column slab s holds the columns kx in [32 s, 32 s + 32) and their partners
-// -kx (slab 0 also holds the self-paired column 128), so every (k, -k) pair of
-// the spectral step lies in one slab. One iteration moves 2 MB between L2 and
-// shared memory per frame.
-//
-// 256-point line FFTs: two register passes, 16-point DFTs over elements 16
-// apart with twiddles w_256^(n2 k1), then 16-point DFTs over contiguous groups
-// written back in natural order. Line stride 257 keeps warps that walk 32
-// consecutive lines bank-conflict free.
+// Gerchberg kernel for 256^2 grids (sm_103a): kernels and launchers. The
+// slab-streamed device code is in fwr_slab.cuh.
 
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -34,250 +11,30 @@
 namespace fwr {
 
 #include "fwr_fft.cuh"
-
-namespace {
-
-constexpr int SN = 256;        // grid size
-constexpr int SL = 64;         // lines per slab
-constexpr int SLS = SN + 1;    // line stride in shared memory
-constexpr int SNT = 512;       // threads per CTA
-constexpr int SH = SN / 2;
-
-__device__ __forceinline__ float2 conjf2(float2 a) { return make_float2(a.x, -a.y); }
-
-// Pass A over the 64 lines: 16-point DFT over n1 of elements 16 n1 + n2,
-// then the twiddle w^(n2 k1) (conjugate for the inverse), in place.
-template <bool INV>
-__device__ __forceinline__ void line_pass_a(float2* Lb, const float2* tw) {
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-        const int t = threadIdx.x + i * SNT;
-        const int line = t % SL, n2 = t / SL;
-        float2* base = Lb + line * SLS + n2;
-        float2 x[16];
-#pragma unroll
-        for (int n1 = 0; n1 < 16; ++n1) x[n1] = base[16 * n1];
-        dft_reg<16, INV>(x);
-#pragma unroll
-        for (int k1 = 1; k1 < 16; ++k1) {
-            const float2 w = tw[n2 * k1];
-            x[k1] = INV ? cmulc(w, x[k1]) : cmul(x[k1], w);
-        }
-#pragma unroll
-        for (int k1 = 0; k1 < 16; ++k1) base[16 * k1] = x[k1];
-    }
-}
-
-// Pass B: 16-point DFT over contiguous groups 16 k1 + n2, natural-order output.
-template <bool INV>
-__device__ __forceinline__ void line_pass_b(float2* Lb) {
-    float2 y[2][16];
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-        const int t = threadIdx.x + i * SNT;
-        const int line = t % SL, k1 = t / SL;
-        const float2* base = Lb + line * SLS + 16 * k1;
-#pragma unroll
-        for (int n2 = 0; n2 < 16; ++n2) y[i][n2] = base[n2];
-        dft_reg<16, INV>(y[i]);
-    }
-    __syncthreads();
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-        const int t = threadIdx.x + i * SNT;
-        const int line = t % SL, k1 = t / SL;
-        float2* base = Lb + line * SLS + k1;
-#pragma unroll
-        for (int k2 = 0; k2 < 16; ++k2) base[16 * k2] = y[i][k2];
-    }
-}
-
-// 256-point FFT of all 64 lines of the slab; ends with a barrier.
-template <bool INV>
-__device__ __forceinline__ void line_fft(float2* Lb, const float2* tw) {
-    line_pass_a<INV>(Lb, tw);
-    __syncthreads();
-    line_pass_b<INV>(Lb);
-    __syncthreads();
-}
-
-// storage column of line j in column slab s: j < 32 -> 32 s + j; j >= 32 ->
-// the partner -(32 s + j - 32), with the self-paired column 128 in place of
-// the duplicate 0 in slab 0
-__device__ __forceinline__ int slab_col(int s, int j) {
-    if (j < 32) return 32 * s + j;
-    const int jj = j - 32;
-    return (s == 0 && jj == 0) ? SH : (SN - 32 * s - jj) & (SN - 1);
-}
-// partner line of line j < 32 in slab s (self-paired for column 0)
-__device__ __forceinline__ int slab_partner(int s, int j) { return (s == 0 && j == 0) ? 0 : 32 + j; }
-
-}  // namespace
+#include "fwr_slab.cuh"
 
 __global__ void __launch_bounds__(SNT, 1)
 slab_kernel(Params<float> p, float2* scratch) {
     extern __shared__ __align__(16) unsigned char smem[];
-    float2* Lb = reinterpret_cast<float2*>(smem);
-    float2* tw = Lb + SL * SLS;
-    float2* A = tw + SN;
-    float2* Tt = A + SN;
-    uint8_t* mask = reinterpret_cast<uint8_t*>(Tt + SN);
-    __shared__ float2 eyv[33];
     __shared__ int s_bad;
-
-    const int tid = threadIdx.x;
-    const int n = p.n, off = p.off, nn = n * n;
-    for (int i = tid; i < SN; i += SNT) {
-        tw[i] = p.tab.tw[i];
-        A[i] = p.tab.A[i];
-        Tt[i] = p.tab.Tt[i];
-    }
-    for (int i = tid; i < nn; i += SNT) mask[i] = p.mask[i];
-    if (tid == 0) s_bad = 0;
-    __syncthreads();
-
+    if (threadIdx.x == 0) s_bad = 0;
+    SlabCtx c;
+    slab_setup(c, smem, p.tab, p.mask, p.n, p.off, p.periodic);
     float2* G = scratch + size_t(blockIdx.x) * SN * SN;
-    const int mode = p.periodic;
+    const int nn = p.n * p.n;
     bool finite = true;
     for (int f = blockIdx.x; f < p.F; f += gridDim.x) {
-        const float* sl = p.slopes + size_t(f) * 2 * nn;
-        const float* ext = p.ext_init ? p.ext_init + size_t(f) * 2 * SN * SN : nullptr;
-        // it = -1: embed; it = 0 .. iters-1: Gerchberg; it = iters: final
-        for (int it = -1; it <= p.iters; ++it) {
-            const bool final = it == p.iters;
-            if (it >= 0) {
-                // ------------------------------------------------ column phase
-                const bool fill = mode == PERIODIC_BEFORE_EACH_FFT || (mode == PERIODIC_FINAL_ONLY && final);
-                for (int s = 0; s < 4; ++s) {
-                    for (int idx = tid; idx < SL * SN; idx += SNT) {
-                        const int m = idx / SL, j = idx % SL;
-                        Lb[j * SLS + m] = __ldcg(G + m * SN + slab_col(s, j));
-                    }
-                    __syncthreads();
-                    line_fft<false>(Lb, tw);
-                    if (fill && tid < 33) {
-                        // Sy(0, kx) of every first-half column (and of column 128 in
-                        // slab 0), read before the in-place spectral updates below
-                        const int j = tid, pj = j < 32 ? slab_partner(s, j) : 32;
-                        const float2 e0 = Lb[j * SLS], e1 = Lb[pj * SLS];
-                        eyv[j] = make_float2(0.5f * (e0.y + e1.y), 0.5f * (e1.x - e0.x));
-                    }
-                    __syncthreads();
-                    const int items = 32 * SN + (s == 0 ? SH + 1 : 0);
-                    for (int q = tid; q < items; q += SNT) {
-                        int j, ky, pj;
-                        if (q < 32 * SN) {
-                            j = q / SN;
-                            ky = q % SN;
-                            pj = slab_partner(s, j);
-                            if (pj == j && ky > SH) continue;  // self-paired column: half the bins
-                        } else {
-                            j = 32;  // column 128 in slab 0, self-paired
-                            ky = q - 32 * SN;
-                            pj = 32;
-                        }
-                        const int kx = slab_col(s, j);
-                        const int kyn = (SN - ky) & (SN - 1), kxn = (SN - kx) & (SN - 1);
-                        const float2 z1 = Lb[j * SLS + ky], z2 = Lb[pj * SLS + kyn];
-                        float2 sx = make_float2(0.5f * (z1.x + z2.x), 0.5f * (z1.y - z2.y));
-                        float2 sy = make_float2(0.5f * (z1.y + z2.y), 0.5f * (z2.x - z1.x));
-                        if (fill) {
-                            // y part of Eq. PC: Sy(ky,kx) -= Sy(0,kx) e^{2 i pi ky / N}
-                            const float2 c = cmul(eyv[j], conjf2(tw[ky]));
-                            sy = make_float2(sy.x - c.x, sy.y - c.y);
-                        }
-                        const float2 gx = cmul(A[kx], Tt[ky]);
-                        const float2 gy = cmul(Tt[kx], A[ky]);
-                        const float* wt = final ? p.tab.wfin : p.tab.iota;
-                        const float w = ky <= SH ? __ldg(wt + ky * SN + kx) : __ldg(wt + kyn * SN + kxn);
-                        float2 ph = cadd(cmulc(gx, sx), cmulc(gy, sy));
-                        ph = make_float2(ph.x * w, ph.y * w);
-                        if (!final) {
-                            const float2 ox = cmul(gx, ph), oy = cmul(gy, ph);
-                            Lb[pj * SLS + kyn] = make_float2(ox.x + oy.y, oy.x - ox.y);
-                            Lb[j * SLS + ky] = make_float2(ox.x - oy.y, ox.y + oy.x);
-                        } else {
-                            Lb[pj * SLS + kyn] = conjf2(ph);
-                            Lb[j * SLS + ky] = ph;
-                        }
-                    }
-                    __syncthreads();
-                    line_fft<true>(Lb, tw);
-                    for (int idx = tid; idx < SL * SN; idx += SNT) {
-                        const int m = idx / SL, j = idx % SL;
-                        __stcg(G + m * SN + slab_col(s, j), Lb[j * SLS + m]);
-                    }
-                    __syncthreads();
-                }
-            }
-            // --------------------------------------------------------- row phase
-            const bool fill_next = !final && (mode == PERIODIC_BEFORE_EACH_FFT ||
-                                              (mode == PERIODIC_FINAL_ONLY && it + 1 == p.iters));
-            for (int b = 0; b < 4; ++b) {
-                const int m0 = SL * b;
-                if (it < 0) {
-                    for (int idx = tid; idx < SL * SN; idx += SNT) {
-                        const int l = idx / SN, c = idx % SN;
-                        const int g = (m0 + l) * SN + c;
-                        Lb[l * SLS + c] = ext ? make_float2(ext[g], ext[SN * SN + g]) : make_float2(0.f, 0.f);
-                    }
-                } else {
-                    for (int idx = tid; idx < SL * SN; idx += SNT) {
-                        const int l = idx / SN, c = idx % SN;
-                        Lb[l * SLS + c] = __ldcg(G + (m0 + l) * SN + c);
-                    }
-                    __syncthreads();
-                    line_fft<true>(Lb, tw);
-                    if (final) {
-                        float* ph = p.phase + size_t(f) * SN * SN;
-                        for (int idx = tid; idx < SL * SN; idx += SNT) {
-                            const int l = idx / SN, c = idx % SN;
-                            ph[(m0 + l) * SN + c] = Lb[l * SLS + c].x;
-                        }
-                        __syncthreads();
-                        continue;
-                    }
-                }
-                __syncthreads();
-                // Algorithm 1 step 4 (and the embedding): measurement in the pupil
-                const int i0 = max(0, m0 - off), i1 = min(n, m0 + SL - off);
-                for (int c = tid; c < (i1 - i0) * n; c += SNT) {
-                    const int i = i0 + c / n, j = c % n;
-                    if (mask[i * n + j]) {
-                        const float vx = sl[i * n + j], vy = sl[nn + i * n + j];
-                        if (it < 0) finite &= isfinite(vx) && isfinite(vy);
-                        Lb[(off + i - m0) * SLS + off + j] = make_float2(vx, vy);
-                    }
-                }
-                __syncthreads();
-                if (fill_next) {
-                    // x part of Eq. PC: 8 lanes per row
-                    const int l = tid >> 3, part = tid & 7;
-                    float s = 0.f;
-                    for (int c = part; c < SN - 1; c += 8) s += Lb[l * SLS + c].x;
-                    s += __shfl_xor_sync(0xffffffffu, s, 1);
-                    s += __shfl_xor_sync(0xffffffffu, s, 2);
-                    s += __shfl_xor_sync(0xffffffffu, s, 4);
-                    if (part == 0) Lb[l * SLS + SN - 1].x = -s;
-                    __syncthreads();
-                }
-                line_fft<false>(Lb, tw);
-                for (int idx = tid; idx < SL * SN; idx += SNT) {
-                    const int l = idx / SN, c = idx % SN;
-                    __stcg(G + (m0 + l) * SN + c, Lb[l * SLS + c]);
-                }
-                __syncthreads();
-            }
-        }
+        finite &= slab_frame(c, p.tab, p.slopes + size_t(f) * 2 * nn,
+                             p.ext_init ? p.ext_init + size_t(f) * 2 * SN * SN : nullptr,
+                             p.phase + size_t(f) * SN * SN, p.iters, G);
+        __syncthreads();
     }
     if (!finite) atomicOr(&s_bad, 1);
     __syncthreads();
-    if (tid == 0 && s_bad) atomicOr(p.status, STATUS_NONFINITE);
+    if (threadIdx.x == 0 && s_bad) atomicOr(p.status, STATUS_NONFINITE);
 }
 
-size_t slab_smem_bytes(int n) {
-    return size_t(SL) * SLS * sizeof(float2) + 3 * size_t(SN) * sizeof(float2) + ((size_t(n) * n + 15) & ~size_t(15));
-}
+size_t slab_smem_bytes(int n) { return slab_layout_bytes(n); }
 
 size_t slab_scratch_elems_per_cta() { return size_t(SN) * SN; }
 

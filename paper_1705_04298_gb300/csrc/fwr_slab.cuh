@@ -1,0 +1,294 @@
+// Device code of the 256^2 slab-streamed Gerchberg kernel (fwr_slab.cu),
+// shared with the ragged-batch kernel (fwr_ragged.cu). Included inside
+// namespace fwr after fwr_fft.cuh.
+#pragma once
+
+// Gerchberg kernel for 256^2 grids (sm_103a): slab-streamed through shared memory.
+//
+// A 256 x 256 complex grid (512 KB) does not fit one SM's shared memory, so
+// each persistent CTA keeps its frame's packed grid Z = sx + i sy in its own
+// area of a global scratch buffer (L2 resident: 512 KB per CTA) and streams
+// it through shared memory in slabs of 64 lines:
+//
+//   row phase, 4 slabs of 64 rows:     inverse row FFTs, reinsertion of the
+//                                      measured slopes (Algorithm 1 step 4),
+//                                      x part of the periodic fill (Eq. PC),
+//                                      forward row FFTs
+//   column phase, 4 slabs of 64 cols:  forward column FFTs, y part of Eq. PC
+//                                      as a spectral correction, the LSQ
+//                                      projection (Sec. 3.3) or the final
+//                                      filter (Eqs. 2-3), inverse column FFTs
+//
+// Column slab s holds the columns kx in [32 s, 32 s + 32) and their partners
+// -kx (slab 0 also holds the self-paired column 128), so every (k, -k) pair of
+// the spectral step lies in one slab. One iteration moves 2 MB between L2 and
+// shared memory per frame.
+//
+// 256-point line FFTs: two register passes, 16-point DFTs over elements 16
+// apart with twiddles w_256^(n2 k1), then 16-point DFTs over contiguous groups
+// written back in natural order. Line stride 257 keeps warps that walk 32
+// consecutive lines bank-conflict free.
+
+namespace {
+
+constexpr int SN = 256;        // grid size
+constexpr int SL = 64;         // lines per slab
+constexpr int SLS = SN + 1;    // line stride in shared memory
+constexpr int SNT = 512;       // threads per CTA
+constexpr int SH = SN / 2;
+
+__device__ __forceinline__ float2 conjf2(float2 a) { return make_float2(a.x, -a.y); }
+
+// Pass A over the 64 lines: 16-point DFT over n1 of elements 16 n1 + n2,
+// then the twiddle w^(n2 k1) (conjugate for the inverse), in place.
+template <bool INV>
+__device__ __forceinline__ void line_pass_a(float2* Lb, const float2* tw) {
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const int t = threadIdx.x + i * SNT;
+        const int line = t % SL, n2 = t / SL;
+        float2* base = Lb + line * SLS + n2;
+        float2 x[16];
+#pragma unroll
+        for (int n1 = 0; n1 < 16; ++n1) x[n1] = base[16 * n1];
+        dft_reg<16, INV>(x);
+#pragma unroll
+        for (int k1 = 1; k1 < 16; ++k1) {
+            const float2 w = tw[n2 * k1];
+            x[k1] = INV ? cmulc(w, x[k1]) : cmul(x[k1], w);
+        }
+#pragma unroll
+        for (int k1 = 0; k1 < 16; ++k1) base[16 * k1] = x[k1];
+    }
+}
+
+// Pass B: 16-point DFT over contiguous groups 16 k1 + n2, natural-order output.
+template <bool INV>
+__device__ __forceinline__ void line_pass_b(float2* Lb) {
+    float2 y[2][16];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const int t = threadIdx.x + i * SNT;
+        const int line = t % SL, k1 = t / SL;
+        const float2* base = Lb + line * SLS + 16 * k1;
+#pragma unroll
+        for (int n2 = 0; n2 < 16; ++n2) y[i][n2] = base[n2];
+        dft_reg<16, INV>(y[i]);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const int t = threadIdx.x + i * SNT;
+        const int line = t % SL, k1 = t / SL;
+        float2* base = Lb + line * SLS + k1;
+#pragma unroll
+        for (int k2 = 0; k2 < 16; ++k2) base[16 * k2] = y[i][k2];
+    }
+}
+
+// 256-point FFT of all 64 lines of the slab; ends with a barrier.
+template <bool INV>
+__device__ __forceinline__ void line_fft(float2* Lb, const float2* tw) {
+    line_pass_a<INV>(Lb, tw);
+    __syncthreads();
+    line_pass_b<INV>(Lb);
+    __syncthreads();
+}
+
+// storage column of line j in column slab s: j < 32 -> 32 s + j; j >= 32 ->
+// the partner -(32 s + j - 32), with the self-paired column 128 in place of
+// the duplicate 0 in slab 0
+__device__ __forceinline__ int slab_col(int s, int j) {
+    if (j < 32) return 32 * s + j;
+    const int jj = j - 32;
+    return (s == 0 && jj == 0) ? SH : (SN - 32 * s - jj) & (SN - 1);
+}
+// partner line of line j < 32 in slab s (self-paired for column 0)
+__device__ __forceinline__ int slab_partner(int s, int j) { return (s == 0 && j == 0) ? 0 : 32 + j; }
+
+}  // namespace
+
+// Shared-memory bytes of the slab path for n lenslets.
+__host__ __device__ __forceinline__ size_t slab_layout_bytes(int n) {
+    return size_t(SL) * SLS * sizeof(float2) + 3 * size_t(SN) * sizeof(float2) + 33 * sizeof(float2) +
+           ((size_t(n) * n + 15) & ~size_t(15));
+}
+
+// Per-CTA state of the slab path for one plan.
+struct SlabCtx {
+    float2* Lb;
+    float2* tw;
+    float2* A;
+    float2* Tt;
+    float2* eyv;
+    uint8_t* mask;
+    int n, off, nn, mode;
+};
+
+// Load a plan's 1-D tables and mask into shared memory; ends with a barrier.
+__device__ __forceinline__ void slab_setup(SlabCtx& c, unsigned char* smem, const Tables<float>& tab,
+                                           const uint8_t* mask_g, int n, int off, int mode) {
+    c.Lb = reinterpret_cast<float2*>(smem);
+    c.tw = c.Lb + SL * SLS;
+    c.A = c.tw + SN;
+    c.Tt = c.A + SN;
+    c.eyv = c.Tt + SN;
+    c.mask = reinterpret_cast<uint8_t*>(c.eyv + 33);
+    c.n = n;
+    c.off = off;
+    c.nn = n * n;
+    c.mode = mode;
+    const int tid = threadIdx.x;
+    for (int i = tid; i < SN; i += SNT) {
+        c.tw[i] = tab.tw[i];
+        c.A[i] = tab.A[i];
+        c.Tt[i] = tab.Tt[i];
+    }
+    for (int i = tid; i < c.nn; i += SNT) c.mask[i] = mask_g[i];
+    __syncthreads();
+}
+
+// One frame through the whole path with the grid in G (this CTA's 256^2
+// scratch area). sl: [2][n][n] slopes; ext: [2][N][N] warm start or nullptr;
+// phase: [N][N] output. Called by every thread; returns false in the threads
+// that saw a non-finite measured slope.
+__device__ __forceinline__ bool slab_frame(const SlabCtx& c, const Tables<float>& tab, const float* sl,
+                                           const float* ext, float* phase, int iters, float2* G) {
+    const int tid = threadIdx.x;
+    float2* const Lb = c.Lb;
+    const float2* const tw = c.tw;
+    const float2* const A = c.A;
+    const float2* const Tt = c.Tt;
+    float2* const eyv = c.eyv;
+    const uint8_t* const mask = c.mask;
+    const int n = c.n, off = c.off, nn = c.nn, mode = c.mode;
+    bool finite = true;
+    // it = -1: embed; it = 0 .. iters-1: Gerchberg; it = iters: final
+    for (int it = -1; it <= iters; ++it) {
+        const bool final = it == iters;
+        if (it >= 0) {
+            // ------------------------------------------------ column phase
+            const bool fill = mode == PERIODIC_BEFORE_EACH_FFT || (mode == PERIODIC_FINAL_ONLY && final);
+            for (int s = 0; s < 4; ++s) {
+                for (int idx = tid; idx < SL * SN; idx += SNT) {
+                    const int m = idx / SL, j = idx % SL;
+                    Lb[j * SLS + m] = __ldcg(G + m * SN + slab_col(s, j));
+                }
+                __syncthreads();
+                line_fft<false>(Lb, tw);
+                if (fill && tid < 33) {
+                    // Sy(0, kx) of every first-half column (and of column 128 in
+                    // slab 0), read before the in-place spectral updates below
+                    const int j = tid, pj = j < 32 ? slab_partner(s, j) : 32;
+                    const float2 e0 = Lb[j * SLS], e1 = Lb[pj * SLS];
+                    eyv[j] = make_float2(0.5f * (e0.y + e1.y), 0.5f * (e1.x - e0.x));
+                }
+                __syncthreads();
+                const int items = 32 * SN + (s == 0 ? SH + 1 : 0);
+                for (int q = tid; q < items; q += SNT) {
+                    int j, ky, pj;
+                    if (q < 32 * SN) {
+                        j = q / SN;
+                        ky = q % SN;
+                        pj = slab_partner(s, j);
+                        if (pj == j && ky > SH) continue;  // self-paired column: half the bins
+                    } else {
+                        j = 32;  // column 128 in slab 0, self-paired
+                        ky = q - 32 * SN;
+                        pj = 32;
+                    }
+                    const int kx = slab_col(s, j);
+                    const int kyn = (SN - ky) & (SN - 1), kxn = (SN - kx) & (SN - 1);
+                    const float2 z1 = Lb[j * SLS + ky], z2 = Lb[pj * SLS + kyn];
+                    float2 sx = make_float2(0.5f * (z1.x + z2.x), 0.5f * (z1.y - z2.y));
+                    float2 sy = make_float2(0.5f * (z1.y + z2.y), 0.5f * (z2.x - z1.x));
+                    if (fill) {
+                        // y part of Eq. PC: Sy(ky,kx) -= Sy(0,kx) e^{2 i pi ky / N}
+                        const float2 c = cmul(eyv[j], conjf2(tw[ky]));
+                        sy = make_float2(sy.x - c.x, sy.y - c.y);
+                    }
+                    const float2 gx = cmul(A[kx], Tt[ky]);
+                    const float2 gy = cmul(Tt[kx], A[ky]);
+                    const float* wt = final ? tab.wfin : tab.iota;
+                    const float w = ky <= SH ? __ldg(wt + ky * SN + kx) : __ldg(wt + kyn * SN + kxn);
+                    float2 ph = cadd(cmulc(gx, sx), cmulc(gy, sy));
+                    ph = make_float2(ph.x * w, ph.y * w);
+                    if (!final) {
+                        const float2 ox = cmul(gx, ph), oy = cmul(gy, ph);
+                        Lb[pj * SLS + kyn] = make_float2(ox.x + oy.y, oy.x - ox.y);
+                        Lb[j * SLS + ky] = make_float2(ox.x - oy.y, ox.y + oy.x);
+                    } else {
+                        Lb[pj * SLS + kyn] = conjf2(ph);
+                        Lb[j * SLS + ky] = ph;
+                    }
+                }
+                __syncthreads();
+                line_fft<true>(Lb, tw);
+                for (int idx = tid; idx < SL * SN; idx += SNT) {
+                    const int m = idx / SL, j = idx % SL;
+                    __stcg(G + m * SN + slab_col(s, j), Lb[j * SLS + m]);
+                }
+                __syncthreads();
+            }
+        }
+        // --------------------------------------------------------- row phase
+        const bool fill_next = !final && (mode == PERIODIC_BEFORE_EACH_FFT ||
+                                          (mode == PERIODIC_FINAL_ONLY && it + 1 == iters));
+        for (int b = 0; b < 4; ++b) {
+            const int m0 = SL * b;
+            if (it < 0) {
+                for (int idx = tid; idx < SL * SN; idx += SNT) {
+                    const int l = idx / SN, c = idx % SN;
+                    const int g = (m0 + l) * SN + c;
+                    Lb[l * SLS + c] = ext ? make_float2(ext[g], ext[SN * SN + g]) : make_float2(0.f, 0.f);
+                }
+            } else {
+                for (int idx = tid; idx < SL * SN; idx += SNT) {
+                    const int l = idx / SN, c = idx % SN;
+                    Lb[l * SLS + c] = __ldcg(G + (m0 + l) * SN + c);
+                }
+                __syncthreads();
+                line_fft<true>(Lb, tw);
+                if (final) {
+                    float* ph = phase;
+                    for (int idx = tid; idx < SL * SN; idx += SNT) {
+                        const int l = idx / SN, c = idx % SN;
+                        ph[(m0 + l) * SN + c] = Lb[l * SLS + c].x;
+                    }
+                    __syncthreads();
+                    continue;
+                }
+            }
+            __syncthreads();
+            // Algorithm 1 step 4 (and the embedding): measurement in the pupil
+            const int i0 = max(0, m0 - off), i1 = min(n, m0 + SL - off);
+            for (int c = tid; c < (i1 - i0) * n; c += SNT) {
+                const int i = i0 + c / n, j = c % n;
+                if (mask[i * n + j]) {
+                    const float vx = sl[i * n + j], vy = sl[nn + i * n + j];
+                    if (it < 0) finite &= isfinite(vx) && isfinite(vy);
+                    Lb[(off + i - m0) * SLS + off + j] = make_float2(vx, vy);
+                }
+            }
+            __syncthreads();
+            if (fill_next) {
+                // x part of Eq. PC: 8 lanes per row
+                const int l = tid >> 3, part = tid & 7;
+                float s = 0.f;
+                for (int c = part; c < SN - 1; c += 8) s += Lb[l * SLS + c].x;
+                s += __shfl_xor_sync(0xffffffffu, s, 1);
+                s += __shfl_xor_sync(0xffffffffu, s, 2);
+                s += __shfl_xor_sync(0xffffffffu, s, 4);
+                if (part == 0) Lb[l * SLS + SN - 1].x = -s;
+                __syncthreads();
+            }
+            line_fft<false>(Lb, tw);
+            for (int idx = tid; idx < SL * SN; idx += SNT) {
+                const int l = idx / SN, c = idx % SN;
+                __stcg(G + (m0 + l) * SN + c, Lb[l * SLS + c]);
+            }
+            __syncthreads();
+        }
+    }
+    return finite;
+}

@@ -43,6 +43,14 @@ SIGNATURES = {
     "fwr_reconstruct_static": (_I, [_P, _P, _I, _I, _P, _I, _P]),
     "fwr_plan_reserve": (_I, [_P, _I]),
     "fwr_fft2": (_I, [_I, _P, _P, _I, _I, _P]),
+    "fwr_batch_create": (_I, [ctypes.POINTER(_P), _P, _I, _P, _I, _I]),
+    "fwr_batch_run": (_I, [_P, _P, _P, _P]),
+    "fwr_batch_schedule": (_I, [_P, _I, _D]),
+    "fwr_batch_autotune": (_I, [_P, _P, _P, _P, ctypes.c_char_p]),
+    "fwr_batch_ctas": (_I, [_P]),
+    "fwr_batch_cost_ratio": (_D, [_P]),
+    "fwr_batch_destroy": (None, [_P]),
+    "fwr_schedule_lpt": (_I, [_P, _I, _I, _P, _P]),
     "fwr_get_status": (_I, [_P]),
     "fwr_status_string": (ctypes.c_char_p, [_I]),
     "fwr_last_error": (ctypes.c_char_p, []),
@@ -210,6 +218,77 @@ class Plan:
     def status(self):
         """Read and clear the sticky device status (synchronises)."""
         return STATUS.get(self._lib.fwr_get_status(self._h))
+
+
+class Batch:
+    """A ragged batch (fwr_batch_*): frames of several plans, one launch.
+
+    plans: list of Plan; frame_plan: sequence of plan indices, one per frame.
+    """
+
+    def __init__(self, plans, frame_plan, iters):
+        lib = load()
+        self._lib = lib
+        self.plans = list(plans)  # the plans must outlive the batch
+        fp = np.ascontiguousarray(np.asarray(frame_plan, dtype=np.int32))
+        arr = (ctypes.c_void_p * len(self.plans))(*[p._h.value for p in self.plans])
+        h = ctypes.c_void_p()
+        _check(lib.fwr_batch_create(ctypes.byref(h), ctypes.cast(arr, ctypes.c_void_p), len(self.plans),
+                                    fp.ctypes.data_as(ctypes.c_void_p), len(fp), int(iters)), "fwr_batch_create")
+        self._h = h
+        self.frame_plan = fp
+        self.iters = int(iters)
+
+    @staticmethod
+    def pointer_table(tensors, device="cuda"):
+        """Device array of the tensors' data pointers (int64)."""
+        import torch
+        return torch.tensor([t.data_ptr() for t in tensors], dtype=torch.int64, device=device)
+
+    def run(self, slopes_ptrs, phase_ptrs, stream=None):
+        """slopes_ptrs / phase_ptrs: int64 CUDA tensors of per-frame device pointers."""
+        _check(self._lib.fwr_batch_run(self._h, _ptr(slopes_ptrs), _ptr(phase_ptrs), _stream(stream)),
+               "fwr_batch_run")
+
+    def schedule(self, ctas, cost_ratio):
+        _check(self._lib.fwr_batch_schedule(self._h, int(ctas), float(cost_ratio)), "fwr_batch_schedule")
+
+    def autotune(self, slopes_ptrs, phase_ptrs, cache_path=None, stream=None):
+        path = None if cache_path is None else str(cache_path).encode()
+        _check(self._lib.fwr_batch_autotune(self._h, _ptr(slopes_ptrs), _ptr(phase_ptrs), _stream(stream), path),
+               "fwr_batch_autotune")
+        return self.ctas, self.cost_ratio
+
+    @property
+    def ctas(self):
+        return self._lib.fwr_batch_ctas(self._h)
+
+    @property
+    def cost_ratio(self):
+        return self._lib.fwr_batch_cost_ratio(self._h)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.fwr_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def schedule_lpt(costs, ctas):
+    """Host-only LPT schedule (fwr_schedule_lpt): returns (cta_off, order)."""
+    lib = load()
+    c = np.ascontiguousarray(np.asarray(costs, dtype=np.float64))
+    off = np.zeros(int(ctas) + 1, dtype=np.int32)
+    order = np.zeros(max(1, len(c)), dtype=np.int32)
+    _check(lib.fwr_schedule_lpt(c.ctypes.data_as(ctypes.c_void_p), len(c), int(ctas),
+                                off.ctypes.data_as(ctypes.c_void_p), order.ctypes.data_as(ctypes.c_void_p)),
+           "fwr_schedule_lpt")
+    return off, order[:len(c)]
 
 
 def fft2(x, inverse=False, out=None, stream=None):
