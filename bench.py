@@ -177,6 +177,107 @@ def cpu_oracle_run(frames_per_core=6):
 
 # ------------------------------------------------------------------ main ----
 
+def _time_launches(fn, flush, reps, torch):
+    """Median CUDA-event time (ms) of fn() over reps launches, L2 flushed before each."""
+    stream = torch.cuda.current_stream()
+    out = []
+    for _ in range(reps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out.append(e0.elapsed_time(e1))
+    return statistics.median(out)
+
+
+def extra_measurements(fwr, synth, torch, flush):
+    """The other workloads of the path, timed the same way (device time, L2
+    flushed): 40x40 at each iteration count, the 16x16 single-frame latency
+    (FP32 and FP64), a ragged 4096-frame batch of 40/64/80/128-lenslet pupils
+    (one graph-captured launch, autotuned schedule) and 128x128 lenslets on a
+    256^2 grid with 10 iterations."""
+    peak = fp32_peak_tflops()
+    res = {}
+    # 40x40 on 128^2, k in {0, 1, 2, 5}
+    sl, _, mask = synth.batch(N_LENSLETS, FRAMES, SEED0, SIGMA, R0, L0)
+    r0p, L0p = synth.pitch_units(N_LENSLETS, R0, L0)
+    plan = fwr.Plan(mask, PAD, fwr.WIENER, SIGMA ** 2, r0p, L0p)
+    s = torch.tensor(sl, dtype=torch.float32, device="cuda")
+    ph = torch.empty((FRAMES, 128, 128), device="cuda")
+    per_k = {}
+    for k in (0, 1, 2, 5):
+        for _ in range(3):
+            plan.reconstruct(s, k, ph)
+        ms = _time_launches(lambda: plan.reconstruct(s, k, ph), flush, 20, torch)
+        tf = flops_per_frame(128, k) * FRAMES / (ms / 1e3) / 1e12
+        per_k[str(k)] = {"frames_per_s": FRAMES / (ms / 1e3), "ms": ms, "tflops": tf, "frac": tf / peak}
+    res["40x40_128grid_per_k"] = per_k
+    # 16x16 on 32^2, one frame, k = 10, LSQ: latency
+    fr = synth.frame(16, 0, 0.05)
+    p16 = fwr.Plan(fr["mask"], 2.0, fwr.LSQ)
+    lat = {}
+    for name, dt, call in (("fp32", torch.float32, p16.reconstruct), ("fp64", torch.float64, p16.reconstruct_f64)):
+        x = torch.tensor(fr["slopes"][None], dtype=dt, device="cuda")
+        y = torch.empty((1, 32, 32), dtype=dt, device="cuda")
+        for _ in range(10):
+            call(x, 10, y)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(200):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            call(x, 10, y)
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1) * 1e3)
+        lat[name] = {"us_median": statistics.median(ts), "us_min": min(ts)}
+    res["16x16_32grid_k10_1frame_latency"] = lat
+    # ragged: 1024 frames each of 40, 64, 80, 128 lenslets (128^2, 128^2, 256^2, 256^2), k = 5
+    sizes = [(40, 3.2), (64, 2.0), (80, 3.2), (128, 2.0)]
+    plans = [fwr.Plan(synth.pupil_mask(n), pad, fwr.LSQ) for n, pad in sizes]
+    rng = np.random.default_rng(2)
+    fp = rng.permutation(np.repeat(np.arange(4), 1024))
+    base = []
+    for pl, (n, _) in enumerate(sizes):
+        b, _, _ = synth.batch(n, 64, 30000 + 100 * pl, 0.05)
+        base.append(torch.tensor(b, dtype=torch.float32, device="cuda"))
+    slopes = [base[pl][i % 64] for i, pl in enumerate(fp)]
+    phases = [torch.empty((plans[pl].N,) * 2, device="cuda") for pl in fp]
+    sp, pp = fwr.Batch.pointer_table(slopes), fwr.Batch.pointer_table(phases)
+    batch = fwr.Batch(plans, fp, 5)
+    tune_path = os.path.join(ROOT, "gpurun_out", "fwr_tune.jsonl")
+    os.makedirs(os.path.dirname(tune_path), exist_ok=True)
+    ctas, ratio = batch.autotune(sp, pp, tune_path)
+    g = torch.cuda.CUDAGraph()
+    cs = torch.cuda.Stream()
+    cs.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.graph(g, stream=cs):
+        batch.run(sp, pp, stream=cs)
+    torch.cuda.synchronize()
+    g.replay()
+    ms = _time_launches(g.replay, flush, 10, torch)
+    fl = sum(flops_per_frame(plans[pl].N, 5) for pl in fp)
+    res["ragged_4096_40-64-80-128_k5"] = {"frames_per_s": 4096 / (ms / 1e3), "ms": ms,
+                                          "tflops": fl / (ms / 1e3) / 1e12, "frac": fl / (ms / 1e3) / 1e12 / peak,
+                                          "launches": 1, "graph": True, "ctas": ctas, "cost_ratio": ratio}
+    # 128x128 lenslets on 256^2, k = 10, frozen-flow frames
+    sl4, _, m4 = synth.frozen_flow(128, 32, 7, 0.05, r0=0.12, L0=25.0)
+    p4 = fwr.Plan(m4, 2.0, fwr.LSQ)
+    s4 = torch.tensor(sl4, dtype=torch.float32, device="cuda").repeat(32, 1, 1, 1)[:1000].contiguous()
+    ph4 = torch.empty((1000, 256, 256), device="cuda")
+    p4.reconstruct(s4, 10, ph4)
+    ms = _time_launches(lambda: p4.reconstruct(s4, 10, ph4), flush, 5, torch)
+    tf = flops_per_frame(256, 10) * 1000 / (ms / 1e3) / 1e12
+    res["128x128_256grid_k10_frozen_flow"] = {"frames_per_s": 1000 / (ms / 1e3), "ms": ms, "tflops": tf,
+                                              "frac": tf / peak}
+    return res
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -226,6 +327,7 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--iters", type=int, default=ITERS)
+    ap.add_argument("--no-extras", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -309,6 +411,10 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_step = t.item()
 
+    extras = None
+    if rank == 0 and not args.no_extras:
+        extras = extra_measurements(fwr, synth, torch, flush)
+
     if rank == 0:
         fl = flops_per_frame(N, k) * FRAMES
         achieved = fl / (ms_per_step / 1000.0) / 1e12
@@ -334,6 +440,7 @@ def main():
             "gpu_launches": gpu_launches,
             "clocks": clk,
             "cpu_baseline": cpu_base,
+            "extras": extras,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:

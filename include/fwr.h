@@ -209,6 +209,50 @@ double fwr_batch_cost_ratio(const fwr_batch* batch);
 void fwr_batch_destroy(fwr_batch* batch);
 
 /*
+ * Learned warm start (the paper has no learned component; this is the
+ * project's addition). A small U-Net predicts the slopes outside the pupil
+ * from the measured ones; passed as ext_init to fwr_reconstruct_ex it lets
+ * one or two Gerchberg iterations approach the result of many.
+ * Definition: input 3 x 32 x 32 (x and y slopes inside the pupil, times 0.5,
+ * and the pupil indicator, on the 128 x 128 grid averaged over 4 x 4 blocks);
+ * 4 levels of widths (w, 2w, 4w, 4w), two 3 x 3 convolutions with bias and
+ * ReLU per level, 2 x 2 average pooling, nearest 2 x upsampling, skip
+ * concatenation [upsampled, skip]; 1 x 1 convolution to 2 channels; the
+ * output divided by 0.5 and repeated over 4 x 4 blocks is the warm start.
+ * BF16 weights and activations, FP32 accumulation, FP32 master weights and
+ * Adam. Weights are a flat FP32 vector, layer by layer (e1a e1b e2a e2b e3a
+ * e3b ba bb d3a d3b d2a d2b d1a d1b out), each W[cout][dy][dx][cin] then the
+ * bias[cout].
+ *
+ * fwr_net_create     width w (1..32), largest batch, optional HOST initial
+ *                    weights (count must equal fwr_net_param_count; NULL:
+ *                    zeros). Allocates all buffers.
+ * fwr_net_forward    plan must have N = 128; slopes_dev [F][2][n][n];
+ *                    ext_init_dev [F][2][128][128] output (F <= largest batch)
+ * fwr_net_gradients  forward, masked MSE against the 4 x 4 block means of
+ *                    target_ext_dev [F][2][128][128] over blocks without pupil
+ *                    cells (last block row/column excluded), backward;
+ *                    optional HOST outputs: the gradient (param_count floats)
+ *                    and the loss. Synchronises `stream`.
+ * fwr_net_train_step fwr_net_gradients then one Adam step (lr; betas 0.9,
+ *                    0.999; eps 1e-8).
+ */
+typedef struct fwr_net fwr_net;
+fwr_status fwr_net_create(fwr_net** out, int width, int max_batch, const float* init_weights, int count);
+void fwr_net_destroy(fwr_net* net);
+int fwr_net_param_count(const fwr_net* net);
+fwr_status fwr_net_get_weights(fwr_net* net, float* host, int count);
+fwr_status fwr_net_set_weights(fwr_net* net, const float* host, int count);
+fwr_status fwr_net_forward(fwr_net* net, const fwr_plan* plan, const float* slopes_dev, int n_frames,
+                           float* ext_init_dev, void* stream);
+fwr_status fwr_net_gradients(fwr_net* net, const fwr_plan* plan, const float* slopes_dev,
+                             const float* target_ext_dev, int n_frames, float* grad_host, float* loss_host,
+                             void* stream);
+fwr_status fwr_net_train_step(fwr_net* net, const fwr_plan* plan, const float* slopes_dev,
+                              const float* target_ext_dev, int n_frames, float lr, float* loss_host,
+                              void* stream);
+
+/*
  * The schedule of ragged batches, on the host only: assign n jobs with
  * costs[i] >= 0 to `ctas` workers, longest first to the least loaded worker.
  * Output: worker c runs order[cta_off[c] .. cta_off[c+1]) (cta_off has

@@ -51,6 +51,14 @@ SIGNATURES = {
     "fwr_batch_cost_ratio": (_D, [_P]),
     "fwr_batch_destroy": (None, [_P]),
     "fwr_schedule_lpt": (_I, [_P, _I, _I, _P, _P]),
+    "fwr_net_create": (_I, [ctypes.POINTER(_P), _I, _I, _P, _I]),
+    "fwr_net_destroy": (None, [_P]),
+    "fwr_net_param_count": (_I, [_P]),
+    "fwr_net_get_weights": (_I, [_P, _P, _I]),
+    "fwr_net_set_weights": (_I, [_P, _P, _I]),
+    "fwr_net_forward": (_I, [_P, _P, _P, _I, _P, _P]),
+    "fwr_net_gradients": (_I, [_P, _P, _P, _P, _I, _P, _P, _P]),
+    "fwr_net_train_step": (_I, [_P, _P, _P, _P, _I, ctypes.c_float, _P, _P]),
     "fwr_get_status": (_I, [_P]),
     "fwr_status_string": (ctypes.c_char_p, [_I]),
     "fwr_last_error": (ctypes.c_char_p, []),
@@ -270,6 +278,84 @@ class Batch:
     def close(self):
         if getattr(self, "_h", None):
             self._lib.fwr_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Net:
+    """The warm-start U-Net (fwr_net_*): width w, largest batch, optional
+    initial weights (flat FP32 vector, layer by layer, W[cout][dy][dx][cin]
+    then bias)."""
+
+    def __init__(self, width, max_batch, weights=None):
+        lib = load()
+        self._lib = lib
+        h = ctypes.c_void_p()
+        if weights is None:
+            _check(lib.fwr_net_create(ctypes.byref(h), int(width), int(max_batch), None, 0), "fwr_net_create")
+        else:
+            w = np.ascontiguousarray(np.asarray(weights, dtype=np.float32))
+            _check(lib.fwr_net_create(ctypes.byref(h), int(width), int(max_batch),
+                                      w.ctypes.data_as(ctypes.c_void_p), len(w)), "fwr_net_create")
+        self._h = h
+        self.width = int(width)
+        self.max_batch = int(max_batch)
+        self.param_count = lib.fwr_net_param_count(h)
+
+    def weights(self):
+        w = np.empty(self.param_count, dtype=np.float32)
+        _check(self._lib.fwr_net_get_weights(self._h, w.ctypes.data_as(ctypes.c_void_p), len(w)),
+               "fwr_net_get_weights")
+        return w
+
+    def set_weights(self, weights):
+        w = np.ascontiguousarray(np.asarray(weights, dtype=np.float32))
+        _check(self._lib.fwr_net_set_weights(self._h, w.ctypes.data_as(ctypes.c_void_p), len(w)),
+               "fwr_net_set_weights")
+
+    def forward(self, plan, slopes, ext_init=None, stream=None):
+        """slopes (F, 2, n, n) float32 CUDA -> warm start (F, 2, 128, 128)."""
+        import torch
+        F = slopes.shape[0]
+        _need(slopes, torch.float32, (F, 2, plan.n, plan.n), "slopes")
+        if ext_init is None:
+            ext_init = torch.empty((F, 2, plan.N, plan.N), dtype=torch.float32, device=slopes.device)
+        _need(ext_init, torch.float32, (F, 2, plan.N, plan.N), "ext_init")
+        _check(self._lib.fwr_net_forward(self._h, plan._h, _ptr(slopes), F, _ptr(ext_init), _stream(stream)),
+               "fwr_net_forward")
+        return ext_init
+
+    def gradients(self, plan, slopes, target_ext, stream=None):
+        """(loss, gradient as a flat float32 array) at the current weights."""
+        import torch
+        F = slopes.shape[0]
+        _need(slopes, torch.float32, (F, 2, plan.n, plan.n), "slopes")
+        _need(target_ext, torch.float32, (F, 2, plan.N, plan.N), "target_ext")
+        g = np.empty(self.param_count, dtype=np.float32)
+        loss = ctypes.c_float()
+        _check(self._lib.fwr_net_gradients(self._h, plan._h, _ptr(slopes), _ptr(target_ext), F,
+                                           g.ctypes.data_as(ctypes.c_void_p), ctypes.byref(loss), _stream(stream)),
+               "fwr_net_gradients")
+        return float(loss.value), g
+
+    def train_step(self, plan, slopes, target_ext, lr, stream=None):
+        import torch
+        F = slopes.shape[0]
+        _need(slopes, torch.float32, (F, 2, plan.n, plan.n), "slopes")
+        _need(target_ext, torch.float32, (F, 2, plan.N, plan.N), "target_ext")
+        loss = ctypes.c_float()
+        _check(self._lib.fwr_net_train_step(self._h, plan._h, _ptr(slopes), _ptr(target_ext), F, float(lr),
+                                            ctypes.byref(loss), _stream(stream)), "fwr_net_train_step")
+        return float(loss.value)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.fwr_net_destroy(self._h)
             self._h = None
 
     def __del__(self):
