@@ -123,20 +123,28 @@ def up2_backward(dout):
 
 # --------------------------------------------------------------- network ---
 
-def forward(params, x, w):
-    """x [B, 32, 32, 3] -> prediction [B, 32, 32, 2] and the cache for backward."""
+def forward(params, x, w, store=None):
+    """x [B, 32, 32, 3] -> prediction [B, 32, 32, 2] and the cache for backward.
+
+    store: optional function applied to every hidden activation as it is kept
+    (the ReLU outputs and the pooled maps), e.g. a rounding to a storage
+    format; the identity when None."""
     P = unpack(params, w)
     cache = {}
+    keep = store if store is not None else (lambda a: a)
 
     def cr(name, h):
         z = conv(h, *P[name])
         cache[name] = (h, z)
-        return np.maximum(z, 0.0)
+        return keep(np.maximum(z, 0.0))
+
+    def pool(a):
+        return keep(avgpool2(a))
 
     s1 = cr("e1b", cr("e1a", x))
-    s2 = cr("e2b", cr("e2a", avgpool2(s1)))
-    s3 = cr("e3b", cr("e3a", avgpool2(s2)))
-    bt = cr("bb", cr("ba", avgpool2(s3)))
+    s2 = cr("e2b", cr("e2a", pool(s1)))
+    s3 = cr("e3b", cr("e3a", pool(s2)))
+    bt = cr("bb", cr("ba", pool(s3)))
     d3 = cr("d3b", cr("d3a", np.concatenate([up2(bt), s3], axis=-1)))
     d2 = cr("d2b", cr("d2a", np.concatenate([up2(d3), s2], axis=-1)))
     d1 = cr("d1b", cr("d1a", np.concatenate([up2(d2), s1], axis=-1)))
