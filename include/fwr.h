@@ -78,6 +78,13 @@ typedef enum {
 
 /* Option keys for fwr_plan_set_option. */
 #define FWR_OPT_PERIODIC 1
+#define FWR_OPT_TRANSFORM 2
+/* Values of FWR_OPT_TRANSFORM: how the FP32 entry points take 2-D transforms. */
+#define FWR_TRANSFORM_FFT 0         /* shared-memory FFT (default) */
+#define FWR_TRANSFORM_DFT_BF16X3 1  /* dense DFT products on the tensor cores with split-BF16
+                                       operands (x = hi + lo, products hi*hi + hi*lo + lo*hi,
+                                       FP32 accumulation); N = 32 or 64 only
+                                       (FWR_ERR_UNSUPPORTED otherwise); about 1e-4 relative error */
 /* Values of FWR_OPT_PERIODIC: where Eq. PC is applied. */
 #define FWR_PERIODIC_BEFORE_EACH_FFT 0 /* before every forward FFT, the final one included (default) */
 #define FWR_PERIODIC_FINAL_ONLY 1      /* once, before the final reconstruction (Algorithm 1 step 5) */
@@ -302,6 +309,15 @@ fwr_status fwr_reconstruct_static(fwr_plan* plan, const float* slopes_dev, int n
  */
 fwr_status fwr_fft2(int N, const float* in_dev, float* out_dev, int n_frames, int inverse,
                     void* stream);
+
+/*
+ * Batched 2-D DFT of n_frames complex N x N grids as dense products on the
+ * tensor cores with split-BF16 operands (the transform of
+ * FWR_TRANSFORM_DFT_BF16X3). Same layouts and sign conventions as fwr_fft2;
+ * N in {32, 64}.
+ */
+fwr_status fwr_dft2_bf16x3(int N, const float* in_dev, float* out_dev, int n_frames, int inverse,
+                           void* stream);
 
 /*
  * Read and clear the plan's sticky device status word. Synchronises the

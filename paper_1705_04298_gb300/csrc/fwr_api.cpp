@@ -265,6 +265,13 @@ int fwr_plan_valid_count(const fwr_plan* p) { return p ? p->nvalid : -1; }
 
 fwr_status fwr_plan_set_option(fwr_plan* p, int key, double value) {
     if (!p) return FWR_ERR_ARG;
+    if (key == FWR_OPT_TRANSFORM) {
+        const int v = int(value);
+        if (double(v) != value || (v != FWR_TRANSFORM_FFT && v != FWR_TRANSFORM_DFT_BF16X3)) return FWR_ERR_ARG;
+        if (v == FWR_TRANSFORM_DFT_BF16X3 && p->N != 32 && p->N != 64) return FWR_ERR_UNSUPPORTED;
+        p->transform = v;
+        return FWR_OK;
+    }
     if (key == FWR_OPT_PERIODIC) {
         const int v = int(value);
         if (double(v) != value || v < FWR_PERIODIC_BEFORE_EACH_FFT || v > FWR_PERIODIC_NONE) return FWR_ERR_ARG;
@@ -301,7 +308,9 @@ fwr_status fwr_reconstruct_ex(fwr_plan* p, const float* slopes, const float* ext
     k.periodic = p->periodic;
     k.status = p->d_status;
     cudaError_t e;
-    if (p->N == 256) {
+    if (p->transform == FWR_TRANSFORM_DFT_BF16X3) {
+        e = fwr::launch_basic_gemm_f32(p->N, k, static_cast<cudaStream_t>(stream));
+    } else if (p->N == 256) {
         if (ext_out || !phase) return FWR_ERR_UNSUPPORTED;
         e = fwr::launch_slab(k, p->d_scratch, p->scratch_ctas, static_cast<cudaStream_t>(stream));
     } else {
@@ -411,12 +420,34 @@ fwr_status fwr_reconstruct_host(fwr_plan* p, const float* slopes_host, int n_fra
     return e == cudaSuccess ? FWR_OK : cuda_fail(e, "D2H phase");
 }
 
+static fwr_status twiddles_for(int N, float2** out);
+
+fwr_status fwr_dft2_bf16x3(int N, const float* in, float* out, int n_frames, int inverse, void* stream) {
+    if (!(N == 32 || N == 64) || n_frames < 0) return FWR_ERR_ARG;
+    if (n_frames == 0) return FWR_OK;
+    if (!in || !out) return FWR_ERR_ARG;
+    float2* tw = nullptr;
+    fwr_status st = twiddles_for(N, &tw);
+    if (st != FWR_OK) return st;
+    cudaError_t e = fwr::launch_dft2_gemm_f32(N, reinterpret_cast<const float2*>(in), reinterpret_cast<float2*>(out),
+                                             n_frames, inverse, tw, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? FWR_OK : cuda_fail(e, "dft2 bf16x3 launch");
+}
+
 fwr_status fwr_fft2(int N, const float* in, float* out, int n_frames, int inverse, void* stream) {
     if (!(N == 16 || N == 32 || N == 64 || N == 128) || n_frames < 0) return FWR_ERR_ARG;
     if (n_frames == 0) return FWR_OK;
     if (!in || !out) return FWR_ERR_ARG;
-    // one twiddle table per (device, N), built in FP64 and kept for the
-    // process lifetime
+    float2* tw = nullptr;
+    fwr_status st = twiddles_for(N, &tw);
+    if (st != FWR_OK) return st;
+    cudaError_t e = fwr::launch_fft2_f32(N, reinterpret_cast<const float2*>(in), reinterpret_cast<float2*>(out),
+                                        n_frames, inverse, tw, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? FWR_OK : cuda_fail(e, "fft2 launch");
+}
+
+// one twiddle table per (device, N), built in FP64 and kept for the process lifetime
+static fwr_status twiddles_for(int N, float2** out) {
     static std::mutex mu;
     static std::map<std::pair<int, int>, float2*> cache;
     int dev = 0;
@@ -440,9 +471,8 @@ fwr_status fwr_fft2(int N, const float* in, float* out, int n_frames, int invers
             tw = it->second;
         }
     }
-    e = fwr::launch_fft2_f32(N, reinterpret_cast<const float2*>(in), reinterpret_cast<float2*>(out), n_frames,
-                             inverse, tw, static_cast<cudaStream_t>(stream));
-    return e == cudaSuccess ? FWR_OK : cuda_fail(e, "fft2 launch");
+    *out = tw;
+    return FWR_OK;
 }
 
 fwr_status fwr_get_status(fwr_plan* p) {

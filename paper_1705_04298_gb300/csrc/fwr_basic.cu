@@ -27,6 +27,7 @@
 namespace fwr {
 
 #include "fwr_fft.cuh"
+#include "fwr_dftgemm.cuh"
 
 template <int N> struct Split;
 template <> struct Split<16> { static constexpr int R1 = 4, R2 = 4, NT = 64; };
@@ -196,7 +197,19 @@ __host__ __device__ constexpr size_t smem_layout_bytes(int n) {
            align16<T>(size_t(n) * n);
 }
 
-template <typename T, int N>
+// extra shared memory of the DFT-GEMM transforms: 4 N^2 split operands and
+// the 6 N^2 split DFT matrix, BF16
+template <int N> __host__ __device__ constexpr size_t gemm_extra_bytes() { return size_t(10) * N * N * 2; }
+
+// 2-D transform of the generic kernel: the shared-memory FFT, or (GEMM) the
+// split-BF16 tensor-core DFT. Both end with a barrier.
+template <int N, int NT, bool INV, bool GEMM, typename V>
+__device__ __forceinline__ void transform2(V* Z, const V* tw, bf16_t* xb, const bf16_t* Fm) {
+    if constexpr (GEMM) dft2_gemm<N, NT, INV>(Z, N + 1, xb, Fm);
+    else fft2<N, NT, INV>(Z, tw);
+}
+
+template <typename T, int N, bool GEMM>
 __global__ void __launch_bounds__(Split<N>::NT)
 basic_kernel(Params<T> p) {
     typedef typename cvec<T>::type V;
@@ -211,6 +224,8 @@ basic_kernel(Params<T> p) {
     uint8_t* mask = reinterpret_cast<uint8_t*>(smem_raw) +
                     align16<T>(size_t(N) * S * sizeof(V) + 3 * size_t(N) * sizeof(V) +
                                2 * size_t(H + 1) * N * sizeof(T));
+    bf16_t* xb = reinterpret_cast<bf16_t*>(smem_raw + smem_layout_bytes<T, N>(p.n));
+    bf16_t* Fm = xb + 4 * N * N;
     __shared__ int s_bad;
 
     const int n = p.n, off = p.off, nn = n * n;
@@ -226,6 +241,10 @@ basic_kernel(Params<T> p) {
     for (int i = threadIdx.x; i < nn; i += NT) mask[i] = p.mask[i];
     if (threadIdx.x == 0) s_bad = 0;
     __syncthreads();
+    if constexpr (GEMM) {
+        dft_matrix_split<N, NT>(Fm, tw);
+        __syncthreads();
+    }
 
     bool finite = true;
     for (int f = blockIdx.x; f < p.F; f += gridDim.x) {
@@ -246,10 +265,10 @@ basic_kernel(Params<T> p) {
                 periodic_fill<N, NT, T>(Z);
                 __syncthreads();
             }
-            fft2<N, NT, false>(Z, tw);
+            transform2<N, NT, false, GEMM>(Z, tw, xb, Fm);
             spectral<N, NT, false, T>(Z, A, Tt, iota);
             __syncthreads();
-            fft2<N, NT, true>(Z, tw);
+            transform2<N, NT, true, GEMM>(Z, tw, xb, Fm);
             reinsert<N, NT>(Z, mask, sl, n, off);
             __syncthreads();
         }
@@ -267,10 +286,10 @@ basic_kernel(Params<T> p) {
             __syncthreads();
         }
         if (p.phase) {
-            fft2<N, NT, false>(Z, tw);
+            transform2<N, NT, false, GEMM>(Z, tw, xb, Fm);
             spectral<N, NT, true, T>(Z, A, Tt, wfin);
             __syncthreads();
-            fft2<N, NT, true>(Z, tw);
+            transform2<N, NT, true, GEMM>(Z, tw, xb, Fm);
             T* ph = p.phase + size_t(f) * N * N;
             for (int idx = threadIdx.x; idx < N * N; idx += NT) ph[idx] = Z[(idx / N) * S + idx % N].x;
         }
@@ -292,11 +311,11 @@ size_t basic_smem_bytes(int N, int elem_bytes, int n) {
     }
 }
 
-template <typename T, int N>
+template <typename T, int N, bool GEMM = false>
 static cudaError_t launch_one(const Params<T>& p, cudaStream_t s) {
     constexpr int NT = Split<N>::NT;
-    const size_t smem = smem_layout_bytes<T, N>(p.n);
-    auto kern = basic_kernel<T, N>;
+    const size_t smem = smem_layout_bytes<T, N>(p.n) + (GEMM ? gemm_extra_bytes<N>() : 0);
+    auto kern = basic_kernel<T, N, GEMM>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per_sm = 0;
@@ -325,6 +344,62 @@ cudaError_t launch_basic_f64(int N, const Params<double>& p, cudaStream_t s) {
         case 16: return launch_one<double, 16>(p, s);
         case 32: return launch_one<double, 32>(p, s);
         case 64: return launch_one<double, 64>(p, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_basic_gemm_f32(int N, const Params<float>& p, cudaStream_t s) {
+    switch (N) {
+        case 32: return launch_one<float, 32, true>(p, s);
+        case 64: return launch_one<float, 64, true>(p, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+// Standalone batched 2-D DFT through the split-BF16 tensor-core products (test entry).
+template <int N, bool INV>
+__global__ void __launch_bounds__(Split<N>::NT)
+dft2_gemm_kernel(const float2* in, float2* out, int F, const float2* twg) {
+    constexpr int NT = Split<N>::NT, S = N + 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* Z = reinterpret_cast<float2*>(smem_raw);
+    float2* tw = Z + N * S;
+    bf16_t* xb = reinterpret_cast<bf16_t*>(smem_raw + align16<float>(size_t(N) * S * 8 + size_t(N) * 8));
+    bf16_t* Fm = xb + 4 * N * N;
+    for (int i = threadIdx.x; i < N; i += NT) tw[i] = twg[i];
+    __syncthreads();
+    dft_matrix_split<N, NT>(Fm, tw);
+    for (int f = blockIdx.x; f < F; f += gridDim.x) {
+        const float2* src = in + size_t(f) * N * N;
+        for (int idx = threadIdx.x; idx < N * N; idx += NT) Z[(idx / N) * S + idx % N] = src[idx];
+        __syncthreads();
+        dft2_gemm<N, NT, INV>(Z, S, xb, Fm);
+        float2* dst = out + size_t(f) * N * N;
+        for (int idx = threadIdx.x; idx < N * N; idx += NT) dst[idx] = Z[(idx / N) * S + idx % N];
+        __syncthreads();
+    }
+}
+
+template <int N>
+static cudaError_t launch_dft2_gemm_n(const float2* in, float2* out, int F, int inverse, const float2* tw,
+                                      cudaStream_t s) {
+    const size_t smem = align16<float>(size_t(N) * (N + 1) * 8 + size_t(N) * 8) + gemm_extra_bytes<N>();
+    auto kern = inverse ? dft2_gemm_kernel<N, true> : dft2_gemm_kernel<N, false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    const int grid = F < 4 * sms ? F : 4 * sms;
+    kern<<<grid, Split<N>::NT, smem, s>>>(in, out, F, tw);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dft2_gemm_f32(int N, const float2* in, float2* out, int F, int inverse, const float2* tw,
+                                 cudaStream_t s) {
+    switch (N) {
+        case 32: return launch_dft2_gemm_n<32>(in, out, F, inverse, tw, s);
+        case 64: return launch_dft2_gemm_n<64>(in, out, F, inverse, tw, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -46,6 +46,12 @@ size_t basic_smem_bytes(int N, int elem_bytes, int n);
 // Generic kernel (fwr_basic.cu): one persistent launch over all frames.
 cudaError_t launch_basic_f32(int N, const Params<float>& p, cudaStream_t s);
 cudaError_t launch_basic_f64(int N, const Params<double>& p, cudaStream_t s);
+// The generic kernel with every 2-D transform done as split-BF16 tensor-core
+// DFT products (N in {32, 64}).
+cudaError_t launch_basic_gemm_f32(int N, const Params<float>& p, cudaStream_t s);
+// Standalone batched split-BF16 DFT (test entry), N in {32, 64}.
+cudaError_t launch_dft2_gemm_f32(int N, const float2* in, float2* out, int F, int inverse, const float2* tw,
+                                 cudaStream_t s);
 
 // 256^2 grids (fwr_slab.cu): the grid lives in a per-CTA global scratch area
 // of slab_scratch_elems_per_cta() float2 and is streamed through shared

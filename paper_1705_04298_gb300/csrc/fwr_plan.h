@@ -30,6 +30,7 @@ void set_last_error(const char* msg);
 
 struct fwr_plan {
     int n = 0, N = 0, off = 0, filter = 0, periodic = FWR_PERIODIC_BEFORE_EACH_FFT, nvalid = 0;
+    int transform = FWR_TRANSFORM_FFT;
     int device = 0;
     double noise_var = 0, r0 = 0, L0 = 0;
     uint8_t* d_mask = nullptr;

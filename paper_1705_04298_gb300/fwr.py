@@ -21,6 +21,9 @@ PERIODIC_BEFORE_EACH_FFT = 0
 PERIODIC_FINAL_ONLY = 1
 PERIODIC_NONE = 2
 OPT_PERIODIC = 1
+OPT_TRANSFORM = 2
+TRANSFORM_FFT = 0
+TRANSFORM_DFT_BF16X3 = 1
 STATIC_SCRATCH_GRIDS = 16
 
 STATUS = {0: "FWR_OK", 1: "FWR_ERR_ARG", 2: "FWR_ERR_UNSUPPORTED", 3: "FWR_ERR_CUDA",
@@ -43,6 +46,7 @@ SIGNATURES = {
     "fwr_reconstruct_static": (_I, [_P, _P, _I, _I, _P, _I, _P]),
     "fwr_plan_reserve": (_I, [_P, _I]),
     "fwr_fft2": (_I, [_I, _P, _P, _I, _I, _P]),
+    "fwr_dft2_bf16x3": (_I, [_I, _P, _P, _I, _I, _P]),
     "fwr_batch_create": (_I, [ctypes.POINTER(_P), _P, _I, _P, _I, _I]),
     "fwr_batch_run": (_I, [_P, _P, _P, _P]),
     "fwr_batch_schedule": (_I, [_P, _I, _D]),
@@ -145,6 +149,11 @@ class Plan:
     def set_periodic(self, mode):
         _check(self._lib.fwr_plan_set_option(self._h, OPT_PERIODIC, float(mode)), "fwr_plan_set_option")
         self.periodic = mode
+
+    def set_transform(self, mode):
+        """TRANSFORM_FFT (default) or TRANSFORM_DFT_BF16X3 (tensor-core split-BF16 DFT, N = 32/64)."""
+        _check(self._lib.fwr_plan_set_option(self._h, OPT_TRANSFORM, float(mode)), "fwr_plan_set_option")
+        self.transform = mode
 
     def close(self):
         if getattr(self, "_h", None):
@@ -375,6 +384,21 @@ def schedule_lpt(costs, ctas):
                                 off.ctypes.data_as(ctypes.c_void_p), order.ctypes.data_as(ctypes.c_void_p)),
            "fwr_schedule_lpt")
     return off, order[:len(c)]
+
+
+def dft2_bf16x3(x, inverse=False, out=None, stream=None):
+    """Batched 2-D DFT (fwr_dft2_bf16x3) of a (F, N, N) complex64 CUDA tensor,
+    N in {32, 64}, through split-BF16 tensor-core products; no scaling."""
+    import torch
+    if x.dtype != torch.complex64 or x.dim() != 3 or x.shape[1] != x.shape[2] or not x.is_cuda:
+        raise ValueError("x must be a (F, N, N) complex64 CUDA tensor")
+    x = x.contiguous()
+    if out is None:
+        out = torch.empty_like(x)
+    lib = load()
+    _check(lib.fwr_dft2_bf16x3(int(x.shape[1]), _ptr(x), _ptr(out), int(x.shape[0]), int(bool(inverse)),
+                               _stream(stream)), "fwr_dft2_bf16x3")
+    return out
 
 
 def fft2(x, inverse=False, out=None, stream=None):
