@@ -39,6 +39,17 @@ constexpr int SH = SN / 2;
 
 __device__ __forceinline__ float2 conjf2(float2 a) { return make_float2(a.x, -a.y); }
 
+// asynchronous global -> shared copies (cp.async), completed by cp_wait_all
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // Pass A over the 64 lines: 16-point DFT over n1 of elements 16 n1 + n2,
 // then the twiddle w^(n2 k1) (conjugate for the inverse), in place.
 template <bool INV>
@@ -108,10 +119,12 @@ __device__ __forceinline__ int slab_partner(int s, int j) { return (s == 0 && j 
 
 }  // namespace
 
-// Shared-memory bytes of the slab path for n lenslets.
+// Shared-memory bytes of the slab path for n lenslets: the slab, the 1-D
+// tables, Sy(0, kx) per column pair, the spectral weights of the current
+// column slab (33 columns x 256 rows) and the mask.
 __host__ __device__ __forceinline__ size_t slab_layout_bytes(int n) {
     return size_t(SL) * SLS * sizeof(float2) + 3 * size_t(SN) * sizeof(float2) + 33 * sizeof(float2) +
-           ((size_t(n) * n + 15) & ~size_t(15));
+           33 * size_t(SN) * sizeof(float) + ((size_t(n) * n + 15) & ~size_t(15));
 }
 
 // Per-CTA state of the slab path for one plan.
@@ -121,6 +134,7 @@ struct SlabCtx {
     float2* A;
     float2* Tt;
     float2* eyv;
+    float* wts;
     uint8_t* mask;
     int n, off, nn, mode;
 };
@@ -133,7 +147,8 @@ __device__ __forceinline__ void slab_setup(SlabCtx& c, unsigned char* smem, cons
     c.A = c.tw + SN;
     c.Tt = c.A + SN;
     c.eyv = c.Tt + SN;
-    c.mask = reinterpret_cast<uint8_t*>(c.eyv + 33);
+    c.wts = reinterpret_cast<float*>(c.eyv + 33);
+    c.mask = reinterpret_cast<uint8_t*>(c.wts + 33 * SN);
     c.n = n;
     c.off = off;
     c.nn = n * n;
@@ -160,6 +175,7 @@ __device__ __forceinline__ bool slab_frame(const SlabCtx& c, const Tables<float>
     const float2* const A = c.A;
     const float2* const Tt = c.Tt;
     float2* const eyv = c.eyv;
+    float* const wts = c.wts;
     const uint8_t* const mask = c.mask;
     const int n = c.n, off = c.off, nn = c.nn, mode = c.mode;
     bool finite = true;
@@ -172,8 +188,20 @@ __device__ __forceinline__ bool slab_frame(const SlabCtx& c, const Tables<float>
             for (int s = 0; s < 4; ++s) {
                 for (int idx = tid; idx < SL * SN; idx += SNT) {
                     const int m = idx / SL, j = idx % SL;
-                    Lb[j * SLS + m] = __ldcg(G + m * SN + slab_col(s, j));
+                    cp_async8(Lb + j * SLS + m, G + m * SN + slab_col(s, j));
                 }
+                {
+                    // spectral weights of the first-half columns: wts[j][ky] at
+                    // (ky, kx) from the half-table (rows 0..N/2; (-ky, -kx) beyond)
+                    const float* wt = final ? tab.wfin : tab.iota;
+                    const int nj = s == 0 ? 33 : 32;
+                    for (int idx = tid; idx < nj * SN; idx += SNT) {
+                        const int j = idx / SN, ky = idx % SN;
+                        const int kx = slab_col(s, j), kxn = (SN - kx) & (SN - 1);
+                        cp_async4(wts + idx, ky <= SH ? wt + ky * SN + kx : wt + ((SN - ky) & (SN - 1)) * SN + kxn);
+                    }
+                }
+                cp_wait_all();
                 __syncthreads();
                 line_fft<false>(Lb, tw);
                 if (fill && tid < 33) {
@@ -198,7 +226,7 @@ __device__ __forceinline__ bool slab_frame(const SlabCtx& c, const Tables<float>
                         pj = 32;
                     }
                     const int kx = slab_col(s, j);
-                    const int kyn = (SN - ky) & (SN - 1), kxn = (SN - kx) & (SN - 1);
+                    const int kyn = (SN - ky) & (SN - 1);
                     const float2 z1 = Lb[j * SLS + ky], z2 = Lb[pj * SLS + kyn];
                     float2 sx = make_float2(0.5f * (z1.x + z2.x), 0.5f * (z1.y - z2.y));
                     float2 sy = make_float2(0.5f * (z1.y + z2.y), 0.5f * (z2.x - z1.x));
@@ -209,8 +237,7 @@ __device__ __forceinline__ bool slab_frame(const SlabCtx& c, const Tables<float>
                     }
                     const float2 gx = cmul(A[kx], Tt[ky]);
                     const float2 gy = cmul(Tt[kx], A[ky]);
-                    const float* wt = final ? tab.wfin : tab.iota;
-                    const float w = ky <= SH ? __ldg(wt + ky * SN + kx) : __ldg(wt + kyn * SN + kxn);
+                    const float w = wts[j * SN + ky];
                     float2 ph = cadd(cmulc(gx, sx), cmulc(gy, sy));
                     ph = make_float2(ph.x * w, ph.y * w);
                     if (!final) {
@@ -245,15 +272,16 @@ __device__ __forceinline__ bool slab_frame(const SlabCtx& c, const Tables<float>
             } else {
                 for (int idx = tid; idx < SL * SN; idx += SNT) {
                     const int l = idx / SN, c = idx % SN;
-                    Lb[l * SLS + c] = __ldcg(G + (m0 + l) * SN + c);
+                    cp_async8(Lb + l * SLS + c, G + (m0 + l) * SN + c);
                 }
+                cp_wait_all();
                 __syncthreads();
                 line_fft<true>(Lb, tw);
                 if (final) {
                     float* ph = phase;
                     for (int idx = tid; idx < SL * SN; idx += SNT) {
                         const int l = idx / SN, c = idx % SN;
-                        ph[(m0 + l) * SN + c] = Lb[l * SLS + c].x;
+                        __stcs(ph + (m0 + l) * SN + c, Lb[l * SLS + c].x);
                     }
                     __syncthreads();
                     continue;
