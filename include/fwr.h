@@ -140,7 +140,9 @@ fwr_status fwr_reconstruct(fwr_plan* plan, const float* slopes_dev, int n_frames
 /*
  * As fwr_reconstruct, with two optional extras (ext_out needs N <= 128).
  *   ext_init_dev  [n_frames][2][N][N] initial slopes used OUTSIDE the pupil
- *                 before the first iteration (a warm start), or NULL for 0
+ *                 before the first iteration (a warm start), or NULL for 0;
+ *                 16-byte aligned (FWR_ERR_ARG otherwise; same for the FP64
+ *                 entry point)
  *   phase_dev     may be NULL (no final reconstruction)
  *   ext_out_dev   [n_frames][2][N][N] output: the extended slopes that enter
  *                 the final reconstruction (after the periodic fill where it
@@ -243,7 +245,20 @@ void fwr_batch_destroy(fwr_batch* batch);
  *                    and the loss. Synchronises `stream`.
  * fwr_net_train_step fwr_net_gradients then one Adam step (lr; betas 0.9,
  *                    0.999; eps 1e-8).
+ * fwr_net_set_option FWR_NET_OPT_CONV: FWR_NET_CONV_AUTO (default) runs the
+ *                    forward 3 x 3 convolutions whose input channel groups are
+ *                    multiples of 16 and output channels multiples of 8 on the
+ *                    tensor cores (implicit GEMM, BF16 in, FP32 accumulate);
+ *                    FWR_NET_CONV_SIMT keeps every convolution on the CUDA
+ *                    cores. Both sum in FP32 and round the stored activation to
+ *                    BF16; they differ only in summation order. Unknown option
+ *                    or value: FWR_ERR_ARG.
+ * fwr_net_tc_layers  how many layers are eligible for the tensor-core forward
+ *                    (-1 for NULL).
  */
+#define FWR_NET_OPT_CONV 1
+#define FWR_NET_CONV_AUTO 0
+#define FWR_NET_CONV_SIMT 1
 typedef struct fwr_net fwr_net;
 fwr_status fwr_net_create(fwr_net** out, int width, int max_batch, const float* init_weights, int count);
 void fwr_net_destroy(fwr_net* net);
@@ -258,6 +273,8 @@ fwr_status fwr_net_gradients(fwr_net* net, const fwr_plan* plan, const float* sl
 fwr_status fwr_net_train_step(fwr_net* net, const fwr_plan* plan, const float* slopes_dev,
                               const float* target_ext_dev, int n_frames, float lr, float* loss_host,
                               void* stream);
+fwr_status fwr_net_set_option(fwr_net* net, int option, int value);
+int fwr_net_tc_layers(const fwr_net* net);
 
 /*
  * The schedule of ragged batches, on the host only: assign n jobs with
@@ -324,6 +341,56 @@ fwr_status fwr_dft2_bf16x3(int N, const float* in_dev, float* out_dev, int n_fra
  * plan's device. FWR_OK, FWR_ERR_NONFINITE or FWR_ERR_TIMEOUT.
  */
 fwr_status fwr_get_status(fwr_plan* plan);
+
+/*
+ * Linear warm start (the project's addition; Algorithm 1, Sec. 3.3, is linear
+ * in the slopes, so the extension the loop reaches after k iterations from a
+ * zero start is one fixed matrix E_k applied to the measured slopes).
+ *
+ * fwr_linws_create   plan: the geometry (its mask fixes the valid cells);
+ *                    rank r: a multiple of 128 in [128, 8192];
+ *                    A_host [2 n_valid][r] and V_host [2 N^2][r], FP32, HOST,
+ *                    a factorisation E ~ A V^T (copied and rounded to BF16; the
+ *                    caller keeps ownership). Slope index j < n_valid is the x
+ *                    slope of the j-th valid lenslet in row-major order, j >=
+ *                    n_valid the y slope of lenslet j - n_valid; the extension
+ *                    index is the flat [2][N][N] index of ext_init.
+ *                    max_batch: largest F. 2 N^2 must be a multiple of 128.
+ * fwr_linws_forward  slopes_dev [F][2][n][n] FP32 -> ext_init_dev [F][2][N][N]
+ *                    FP32 (16-byte aligned) = (X A) V^T with X the gathered
+ *                    slopes, on the tcgen05 tensor cores (BF16 operands, FP32
+ *                    accumulation; X A rounded to BF16). Asynchronous on
+ *                    `stream`; a pipeline wait that runs out is recorded and
+ *                    reported by fwr_linws_status (synchronises the device).
+ *                    The result feeds fwr_reconstruct_ex as ext_init.
+ * fwr_linws_reconstruct
+ *                    the warm start and the reconstruction in one call:
+ *                    fwr_linws_forward into a BF16 buffer owned by `ws`
+ *                    ([max_batch][2 N^2], allocated at creation), then the
+ *                    fused kernel of fwr_reconstruct_ex reading it (iters
+ *                    0..64, phase_dev [F][N][N]). `plan` must have the grid and
+ *                    the pupil mask `ws` was created with (its filter may
+ *                    differ); FWR_ERR_ARG otherwise, FWR_ERR_UNSUPPORTED for
+ *                    plans that do not take the fused path (N = 256, the
+ *                    DFT-GEMM transform). Asynchronous on `stream`.
+ * fwr_gemm_bf16_tc   the tensor-core GEMM on its own (synchronous): D [M][N]
+ *                    FP32 = A [M][K] B[N][K]^T, A and B BF16 row-major device
+ *                    arrays (16-byte aligned), K a positive multiple of 8, N a
+ *                    multiple of 128; FWR_ERR_TIMEOUT if a wait ran out.
+ * The GEMM kernel allocates up to 512 TMEM columns per CTA (one CTA per SM);
+ * it is not meant to share an SM with other TMEM users on another stream.
+ */
+typedef struct fwr_linws fwr_linws;
+fwr_status fwr_linws_create(fwr_linws** out, const fwr_plan* plan, int rank, const float* A_host,
+                            const float* V_host, int max_batch);
+void fwr_linws_destroy(fwr_linws* ws);
+int fwr_linws_valid_count(const fwr_linws* ws);
+fwr_status fwr_linws_forward(fwr_linws* ws, const float* slopes_dev, int n_frames, float* ext_init_dev,
+                             void* stream);
+fwr_status fwr_linws_reconstruct(fwr_linws* ws, fwr_plan* plan, const float* slopes_dev, int n_frames,
+                                 int iters, float* phase_dev, void* stream);
+fwr_status fwr_linws_status(fwr_linws* ws);
+fwr_status fwr_gemm_bf16_tc(const void* A_dev, const void* B_dev, int M, int N, int K, float* D_dev, void* stream);
 
 /* Static, human-readable name of a status code. */
 const char* fwr_status_string(fwr_status status);

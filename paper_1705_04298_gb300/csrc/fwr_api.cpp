@@ -214,6 +214,7 @@ fwr_status fwr_plan_create(fwr_plan** out, int n, double pad_factor, const uint8
     }
     std::vector<uint8_t> m(size_t(n) * n);
     for (int i = 0; i < n * n; ++i) m[i] = pupil_mask[i] ? 1 : 0;
+    p->h_mask = m;
     fwr_status st = FWR_OK;
     if ((e = cudaMalloc(&p->d_mask, m.size())) != cudaSuccess ||
         (e = cudaMemcpy(p->d_mask, m.data(), m.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
@@ -289,10 +290,14 @@ static fwr_status check_call(const fwr_plan* p, const void* slopes, int n_frames
     return FWR_OK;
 }
 
+// the warm start is read with 16-byte vector loads (NULL passes)
+static bool aligned16(const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15u) == 0; }
+
 fwr_status fwr_reconstruct_ex(fwr_plan* p, const float* slopes, const float* ext_init, int n_frames, int iters,
                               float* phase, float* ext_out, void* stream) {
     fwr_status st = check_call(p, slopes, n_frames, iters, phase, ext_out);
     if (st != FWR_OK) return st;
+    if (!aligned16(ext_init)) return FWR_ERR_ARG;
     if (n_frames == 0) return FWR_OK;
     fwr::Params<float> k;
     k.tab = view(p->f32);
@@ -365,6 +370,7 @@ fwr_status fwr_reconstruct_f64(fwr_plan* p, const double* slopes, const double* 
                                double* phase, double* ext_out, void* stream) {
     fwr_status st = check_call(p, slopes, n_frames, iters, phase, ext_out);
     if (st != FWR_OK) return st;
+    if (!aligned16(ext_init)) return FWR_ERR_ARG;
     if (p->N > 64) return FWR_ERR_UNSUPPORTED;
     if (n_frames == 0) return FWR_OK;
     fwr::Params<double> k;
@@ -506,3 +512,22 @@ const char* fwr_status_string(fwr_status s) {
 const char* fwr_last_error(void) { return g_last_error; }
 
 }  // extern "C"
+
+cudaError_t fwr::launch_warm_bf16(fwr_plan* p, const float* slopes, const uint16_t* ext_init_h, int n_frames,
+                                  int iters, float* phase, cudaStream_t s) {
+    if (p->transform != FWR_TRANSFORM_FFT || p->N == 256 || !fwr::fused_supported(p->N, 4, p->n))
+        return cudaErrorNotSupported;
+    fwr::Params<float> k;
+    k.tab = view(p->f32);
+    k.mask = p->d_mask;
+    k.slopes = slopes;
+    k.ext_init_h = ext_init_h;
+    k.phase = phase;
+    k.n = p->n;
+    k.off = p->off;
+    k.F = n_frames;
+    k.iters = iters;
+    k.periodic = p->periodic;
+    k.status = p->d_status;
+    return fwr::launch_fused_f32(p->N, k, s);
+}

@@ -24,6 +24,7 @@ fused_kernel(Params<T> p) {
     for (int f = blockIdx.x; f < p.F; f += gridDim.x) {
         finite &= fused_frame<T, N>(c, p.slopes + size_t(f) * 2 * nn,
                                     p.ext_init ? p.ext_init + size_t(f) * 2 * N * N : nullptr,
+                                    p.ext_init_h ? p.ext_init_h + size_t(f) * 2 * N * N : nullptr,
                                     p.phase ? p.phase + size_t(f) * N * N : nullptr,
                                     p.ext_out ? p.ext_out + size_t(f) * 2 * N * N : nullptr, p.iters);
         __syncthreads();

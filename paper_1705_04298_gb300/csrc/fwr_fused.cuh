@@ -79,6 +79,33 @@ __device__ __forceinline__ void store4(double* d, double a, double b, double c, 
     reinterpret_cast<double2*>(d)[1] = make_double2(c, e);
 }
 
+// four adjacent values of a 16-byte-aligned row, read once (streaming)
+__device__ __forceinline__ void load_row4(const float* p, float* v) {
+    const float4 a = __ldcs(reinterpret_cast<const float4*>(p));
+    v[0] = a.x;
+    v[1] = a.y;
+    v[2] = a.z;
+    v[3] = a.w;
+}
+__device__ __forceinline__ void load_row4(const double* p, double* v) {
+    const double2 a = __ldcs(reinterpret_cast<const double2*>(p)), b = __ldcs(reinterpret_cast<const double2*>(p) + 1);
+    v[0] = a.x;
+    v[1] = a.y;
+    v[2] = b.x;
+    v[3] = b.y;
+}
+
+// four adjacent BF16 values (8-byte aligned; a BF16 value is the upper half
+// of the FP32 with the same bits, so the widening is exact)
+template <typename T>
+__device__ __forceinline__ void load_row4(const uint16_t* p, T* v) {
+    const uint2 a = __ldcs(reinterpret_cast<const uint2*>(p));
+    v[0] = T(__uint_as_float(a.x << 16));
+    v[1] = T(__uint_as_float(a.x & 0xFFFF0000u));
+    v[2] = T(__uint_as_float(a.y << 16));
+    v[3] = T(__uint_as_float(a.y & 0xFFFF0000u));
+}
+
 // four adjacent cells (16-byte aligned) in and out
 __device__ __forceinline__ void load4(const float2* p, float2* x) {
     const float4 a = reinterpret_cast<const float4*>(p)[0], b = reinterpret_cast<const float4*>(p)[1];
@@ -301,8 +328,8 @@ __device__ __forceinline__ void fused_setup(FusedCtx<T, N>& c, unsigned char* sm
 // extended slopes or nullptr. Called by every thread; returns false in the
 // threads that saw a non-finite measured slope.
 template <typename T, int N>
-__device__ __forceinline__ bool fused_frame(const FusedCtx<T, N>& c, const T* sl, const T* ext, T* phase,
-                                            T* ext_out, int iters) {
+__device__ __forceinline__ bool fused_frame(const FusedCtx<T, N>& c, const T* sl, const T* ext,
+                                            const uint16_t* exth, T* phase, T* ext_out, int iters) {
     typedef typename cvec<T>::type V;
     constexpr int R = N / 4, NT = 4 * N, H = N / 2, S = Layout<T, N>::S;
     const int tid = threadIdx.x;
@@ -331,6 +358,27 @@ __device__ __forceinline__ bool fused_frame(const FusedCtx<T, N>& c, const T* sl
     const T* const wfn = c.wfn;
     const T half = T(0.5);
     bool finite = true;
+    const bool warm = ext || exth;
+    if (warm) {
+        // warm start: coalesced 4-wide loads of both channels, staged in Z
+        // (free between frames) as complex cells
+        for (int q = tid; q < N * N / 4; q += NT) {
+            const int rr = q / (N / 4), cc = 4 * (q - rr * (N / 4));
+            T ex[4], ey[4];
+            if (ext) {
+                load_row4(ext + rr * N + cc, ex);
+                load_row4(ext + N * N + rr * N + cc, ey);
+            } else {
+                load_row4(exth + rr * N + cc, ex);
+                load_row4(exth + N * N + rr * N + cc, ey);
+            }
+            V* const zp = Z + rr * S + cc;
+            zp[0] = mk(ex[0], ey[0]);
+            zp[1] = mk(ex[1], ey[1]);
+            zp[2] = mk(ex[2], ey[2]);
+            zp[3] = mk(ex[3], ey[3]);
+        }
+    }
     for (int c = tid; c < nn; c += NT) {
         if (mask[c]) {
             const int i = c / n, j = c - i * n;
@@ -347,13 +395,14 @@ __device__ __forceinline__ bool fused_frame(const FusedCtx<T, N>& c, const T* sl
     for (int n1 = 0; n1 < R; ++n1) {
         if (pmask & (1u << n1)) {
             x[n1] = s0row[4 * n1];
-        } else if (ext) {
-            const int c = r * N + 4 * n1 + n2;
-            x[n1] = mk(ext[c], ext[N * N + c]);
+        } else if (warm) {
+            x[n1] = rowp[4 * n1];
         } else {
             x[n1] = mk(T(0), T(0));
         }
     }
+    // the passes below overwrite Z
+    if (warm) __syncthreads();
 
     for (int it = 0; it <= iters; ++it) {
         const bool final = it == iters;

@@ -25,13 +25,14 @@ template <typename T> struct Tables {
 
 template <typename T> struct Params {
     Tables<T> tab;
-    const uint8_t* mask;  // [n n] device copy of the pupil mask
-    const T* slopes;      // [F][2][n][n]
-    const T* ext_init;    // [F][2][N][N] or nullptr
-    T* phase;             // [F][N][N] or nullptr
-    T* ext_out;           // [F][2][N][N] or nullptr
-    int n, off, F, iters, periodic;
-    unsigned* status;     // sticky device status bits
+    const uint8_t* mask = nullptr;       // [n n] device copy of the pupil mask
+    const T* slopes = nullptr;           // [F][2][n][n]
+    const T* ext_init = nullptr;         // [F][2][N][N] or nullptr
+    const uint16_t* ext_init_h = nullptr;  // the same in BF16 (bit patterns; fused kernel only) or nullptr
+    T* phase = nullptr;                  // [F][N][N] or nullptr
+    T* ext_out = nullptr;                // [F][2][N][N] or nullptr
+    int n = 0, off = 0, F = 0, iters = 0, periodic = 0;
+    unsigned* status = nullptr;          // sticky device status bits
 };
 
 // Where Eq. PC is applied (same values as FWR_PERIODIC_* in fwr.h).

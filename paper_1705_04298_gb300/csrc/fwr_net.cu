@@ -15,7 +15,11 @@
 //            over 4 x 4 blocks it is the warm start outside the pupil
 // Storage: activations NHWC in BF16, weights W[cout][dy][dx][cin] in BF16
 // (FP32 master copy for Adam), every sum accumulated in FP32, gradients of
-// activations in FP32. All kernels are SIMT (CUDA cores).
+// activations in FP32. The forward 3 x 3 convolutions whose input channel
+// groups are multiples of 16 (and output channels of 8) run on the tensor
+// cores as implicit GEMMs (mma.sync m16n8k16, BF16 in, FP32 accumulate); the
+// first and last layers, the backward pass and the small elementwise kernels
+// are SIMT.
 
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -135,6 +139,157 @@ __global__ void k_conv_fwd(const bf16* A, int ca, bool upA, const bf16* Bt, int 
             if (out_bf) out_bf[o] = __float2bfloat16(v);
             else out_f[o] = v;
         }
+    }
+}
+
+// ---------------------------------------------- tensor-core convolution --
+//
+// Implicit GEMM: rows = output pixels, columns = output channels, reduction
+// K = 9 cin ordered (tap, channel). A CTA of 4 warps owns TC_TM consecutive
+// output pixels in (image, row, column) order, i.e. TC_TM / W whole rows; it
+// stages those rows with one halo row above and below and one zero column on
+// each side, channels [A (upsampled when upA) | B] with 8 padding channels per
+// pixel (an odd number of 16-byte units per pixel keeps the 8 row reads of an
+// ldmatrix on distinct banks). Each warp computes 32 pixels (two m16 tiles) by
+// 8 NT channels; A fragments come from the halo with ldmatrix, B fragments
+// from the packed weights (one 8-byte load per lane per n8 tile). A tap that
+// falls above the first or below the last row of its image reads a zero
+// block instead; the zero columns cover the left and right edges.
+
+constexpr int TC_TM = 128, TC_THREADS = 128;
+
+__device__ __forceinline__ void ldsm_x4(uint32_t (&a)[4], uint32_t addr) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3])
+                 : "r"(addr));
+}
+
+__device__ __forceinline__ void mma_16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// Shared-memory bytes of k_conv_tc for a layer (W = H)
+inline size_t tc_smem_bytes(int H, int cin) {
+    return size_t(TC_TM / H + 2) * (H + 2) * (cin + 8) * sizeof(bf16) + 32;
+}
+
+// Packed weights of one 3 x 3 layer: Wp[(kc * cout / 8 + nt) * 32 + lane] holds
+// the two B-fragment registers of lane (g, t) = (lane / 4, lane % 4) for the
+// reduction chunk kc = tap * cin / 16 + c0 / 16 and the n8 tile nt:
+// {W[co][tap][c0 + 2t, c0 + 2t + 1], W[co][tap][c0 + 8 + 2t, c0 + 9 + 2t]},
+// co = 8 nt + g.
+__global__ void k_pack_tc(const bf16* Wb, int cin, int cout, uint2* Wp) {
+    const int ntt = cout / 8, kcs = cin / 16;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 9 * kcs * ntt * 32) return;
+    const int lane = i & 31, nt = (i >> 5) % ntt, kc = (i >> 5) / ntt;
+    const int tap = kc / kcs, c0 = (kc % kcs) * 16;
+    const int co = nt * 8 + (lane >> 2), t = lane & 3;
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(Wb + (size_t(co) * 9 + tap) * cin + c0 + 2 * t);
+    Wp[i] = make_uint2(src[0], src[4]);
+}
+
+template <int NT>
+__global__ void __launch_bounds__(TC_THREADS) k_conv_tc(const bf16* __restrict__ A, int ca, int upA,
+                                                        const bf16* __restrict__ Bs, int cb, int H,
+                                                        const uint2* __restrict__ Wp, const float* __restrict__ bias,
+                                                        int cout, int relu, int npix, bf16* __restrict__ out) {
+    extern __shared__ __align__(16) bf16 halo[];
+    const int W = H, cin = ca + cb, PS = cin + 8, RW = W + 2, rows = TC_TM / W + 2;
+    const int P0 = blockIdx.x * TC_TM, g0 = P0 / W, grows = npix / W;
+    const int zoff = rows * RW * PS;
+    const int cv = cin >> 3;
+    for (int i = threadIdx.x; i < rows * RW * cv; i += TC_THREADS) {
+        const int v = i % cv, c = (i / cv) % RW, r = i / (cv * RW);
+        const int gr = g0 - 1 + r, x = c - 1, ch = v * 8;
+        uint4 val = make_uint4(0u, 0u, 0u, 0u);
+        if (gr >= 0 && gr < grows && x >= 0 && x < W) {
+            if (ch < ca) {
+                size_t pix = size_t(gr) * W + x;
+                if (upA) {
+                    const int b = gr / H, y = gr - b * H;
+                    pix = (size_t(b) * (H / 2) + y / 2) * (W / 2) + x / 2;
+                }
+                val = __ldg(reinterpret_cast<const uint4*>(A + pix * ca + ch));
+            } else {
+                val = __ldg(reinterpret_cast<const uint4*>(Bs + (size_t(gr) * W + x) * cb + (ch - ca)));
+            }
+        }
+        *reinterpret_cast<uint4*>(halo + (r * RW + c) * PS + ch) = val;
+    }
+    if (threadIdx.x < 4) reinterpret_cast<uint2*>(halo + zoff)[threadIdx.x] = make_uint2(0u, 0u);
+    __syncthreads();
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int kh = (lane >> 4) * 8;
+    const uint32_t sbase = uint32_t(__cvta_generic_to_shared(halo));
+    int hoff[2], yf[2];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const int p = P0 + warp * 32 + j * 16 + (lane & 15);
+        const int gr = p / W, x = p - gr * W, y = gr % H;
+        hoff[j] = ((gr - g0) * RW + x) * PS + kh;
+        yf[j] = (y == 0 ? 1 : 0) | (y == H - 1 ? 2 : 0);
+    }
+    float acc[2][NT][4];
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt) acc[j][nt][0] = acc[j][nt][1] = acc[j][nt][2] = acc[j][nt][3] = 0.f;
+
+    const int ntt = cout / 8;
+    const uint2* wp = Wp + size_t(blockIdx.y) * NT * 32 + lane;
+    int kc = 0;
+    for (int dy = 0; dy < 3; ++dy) {
+        bool ok[2];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) ok[j] = !((dy == 0 && (yf[j] & 1)) || (dy == 2 && (yf[j] & 2)));
+        for (int dx = 0; dx < 3; ++dx) {
+            uint32_t ad[2], inc[2];
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                ad[j] = sbase + 2u * uint32_t(ok[j] ? hoff[j] + (dy * RW + dx) * PS : zoff + kh);
+                inc[j] = ok[j] ? 32u : 0u;
+            }
+            for (int c0 = 0; c0 < cin; c0 += 16, ++kc) {
+                uint32_t a[2][4];
+                ldsm_x4(a[0], ad[0]);
+                ldsm_x4(a[1], ad[1]);
+                ad[0] += inc[0];
+                ad[1] += inc[1];
+                const uint2* wk = wp + size_t(kc) * ntt * 32;
+#pragma unroll
+                for (int nt = 0; nt < NT; ++nt) {
+                    const uint2 b = __ldg(wk + nt * 32);
+                    mma_16816(acc[0][nt], a[0], b.x, b.y);
+                    mma_16816(acc[1][nt], a[1], b.x, b.y);
+                }
+            }
+        }
+    }
+
+    const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt) {
+        const int co = (blockIdx.y * NT + nt) * 8 + 2 * t;
+        const float b0 = bias[co], b1 = bias[co + 1];
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+                const int p = P0 + warp * 32 + j * 16 + g + 8 * hh;
+                if (p >= npix) continue;
+                float v0 = acc[j][nt][2 * hh] + b0, v1 = acc[j][nt][2 * hh + 1] + b1;
+                if (relu) {
+                    v0 = fmaxf(v0, 0.f);
+                    v1 = fmaxf(v1, 0.f);
+                }
+                *reinterpret_cast<__nv_bfloat162*>(out + size_t(p) * cout + co) = __floats2bfloat162_rn(v0, v1);
+            }
     }
 }
 
@@ -326,6 +481,8 @@ struct Layer {
     int ca, cb, cout, k, H;   // inputs: A (ca), B (cb); output channels; kernel; resolution
     bool upA, relu;
     size_t woff, boff;        // offsets in the flat parameter vector
+    bool tc;                  // forward on the tensor cores (k_conv_tc)
+    size_t poff;              // offset of the packed weights (uint2 units)
 };
 
 inline unsigned blocks(size_t n, int t) { return unsigned((n + t - 1) / t); }
@@ -341,6 +498,9 @@ struct fwr_net {
     size_t nparam = 0;
     float* W = nullptr;   // FP32 master weights (flat)
     bf16* Wb = nullptr;   // BF16 copy used by the kernels
+    uint2* Wp = nullptr;  // BF16 weights of the tensor-core layers in fragment order
+    size_t npacked = 0;   // uint2 count of Wp
+    int conv = FWR_NET_CONV_AUTO;
     float *G = nullptr, *M = nullptr, *V = nullptr;
     int step = 0;
     // activations (BF16) and their gradients (FP32), one per layer output
@@ -379,15 +539,52 @@ void build_layers(fwr_net* n) {
         pos += size_t(x.co) * x.k * x.k * (x.ca + x.cb);
         L.boff = pos;
         pos += x.co;
+        // tensor-core forward: whole 16-channel reduction chunks from one
+        // input, n8 output tiles, 32-bit aligned weight rows, whole rows per CTA
+        L.tc = x.k == 3 && x.ca % 16 == 0 && x.cb % 16 == 0 && x.co % 8 == 0 && L.woff % 2 == 0 &&
+               TC_TM % x.H == 0;
+        L.poff = n->npacked;
+        if (L.tc) n->npacked += size_t(9) * (x.ca + x.cb) * x.co / 4;
         n->layers.push_back(L);
     }
     n->nparam = pos;
+}
+
+int tc_nt(int cout) {
+    const int ntt = cout / 8;
+    return ntt % 8 == 0 ? 8 : ntt % 4 == 0 ? 4 : ntt % 2 == 0 ? 2 : 1;
+}
+
+// BF16 weights -> fragment order for every tensor-core layer
+cudaError_t pack_weights(fwr_net* n, cudaStream_t s) {
+    for (const Layer& L : n->layers) {
+        if (!L.tc) continue;
+        const int cin = L.ca + L.cb;
+        const size_t cnt = size_t(9) * cin * L.cout / 4;
+        k_pack_tc<<<blocks(cnt, 256), 256, 0, s>>>(n->Wb + L.woff, cin, L.cout, n->Wp + L.poff);
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t conv_fwd(fwr_net* n, int li, const bf16* A, const bf16* B, int Bn, bf16* out_bf, float* out_f,
                      cudaStream_t s) {
     const Layer& L = n->layers[li];
     const int cin = L.ca + L.cb, RW = L.H + 2 * (L.k / 2);
+    if (L.tc && out_bf && n->conv == FWR_NET_CONV_AUTO) {
+        const int npix = Bn * L.H * L.H, nt = tc_nt(L.cout);
+        const dim3 grid(unsigned((npix + TC_TM - 1) / TC_TM), unsigned(L.cout / (8 * nt)));
+        const size_t sm = tc_smem_bytes(L.H, cin);
+        const uint2* wp = n->Wp + L.poff;
+        const float* bias = n->W + L.boff;
+        const int up = L.upA ? 1 : 0, relu = L.relu ? 1 : 0;
+        switch (nt) {
+            case 8: k_conv_tc<8><<<grid, TC_THREADS, sm, s>>>(A, L.ca, up, B, L.cb, L.H, wp, bias, L.cout, relu, npix, out_bf); break;
+            case 4: k_conv_tc<4><<<grid, TC_THREADS, sm, s>>>(A, L.ca, up, B, L.cb, L.H, wp, bias, L.cout, relu, npix, out_bf); break;
+            case 2: k_conv_tc<2><<<grid, TC_THREADS, sm, s>>>(A, L.ca, up, B, L.cb, L.H, wp, bias, L.cout, relu, npix, out_bf); break;
+            default: k_conv_tc<1><<<grid, TC_THREADS, sm, s>>>(A, L.ca, up, B, L.cb, L.H, wp, bias, L.cout, relu, npix, out_bf); break;
+        }
+        return cudaGetLastError();
+    }
     const size_t smem = size_t(L.k) * RW * cin * sizeof(float);
     if (L.k == 3)
         k_conv_fwd<3><<<Bn * L.H, 256, smem, s>>>(A, L.ca, L.upA, B, L.cb, L.H, L.H, n->Wb + L.woff, n->W + L.boff,
@@ -505,6 +702,7 @@ cudaError_t backward(fwr_net* n, int Bn, cudaStream_t s) {
 void free_net(fwr_net* n) {
     cudaFree(n->W);
     cudaFree(n->Wb);
+    cudaFree(n->Wp);
     cudaFree(n->G);
     cudaFree(n->M);
     cudaFree(n->V);
@@ -561,6 +759,7 @@ fwr_status fwr_net_create(fwr_net** out, int width, int max_batch, const float* 
     };
     falloc(&n->W, n->nparam);
     balloc(&n->Wb, n->nparam);
+    if (e == cudaSuccess && n->npacked) e = cudaMalloc(&n->Wp, n->npacked * sizeof(uint2));
     falloc(&n->G, n->nparam);
     falloc(&n->M, n->nparam);
     falloc(&n->V, n->nparam);
@@ -593,6 +792,7 @@ fwr_status fwr_net_create(fwr_net** out, int width, int max_batch, const float* 
         e = cudaMemcpy(n->W, h.data(), n->nparam * sizeof(float), cudaMemcpyHostToDevice);
         if (e == cudaSuccess) k_to_bf16<<<blocks(n->nparam, 256), 256>>>(n->W, int(n->nparam), n->Wb);
         if (e == cudaSuccess) e = cudaGetLastError();
+        if (e == cudaSuccess) e = pack_weights(n, 0);
         if (e == cudaSuccess) e = cudaDeviceSynchronize();
     }
     // the convolution kernels stage K rows of (H + 2) pixels x channels as floats
@@ -602,7 +802,21 @@ fwr_status fwr_net_create(fwr_net** out, int width, int max_batch, const float* 
         fwd_smem = std::max(fwd_smem, rw * (L.ca + L.cb));
         dgrad_smem = std::max(dgrad_smem, rw * L.cout);
     }
+    size_t tc_smem = 0;
+    for (const Layer& L : n->layers)
+        if (L.tc) tc_smem = std::max(tc_smem, tc_smem_bytes(L.H, L.ca + L.cb));
     if (fwd_smem > 227 * 1024 || dgrad_smem > 227 * 1024) e = cudaErrorInvalidValue;
+    if (tc_smem > 227 * 1024) {
+        for (Layer& L : n->layers) L.tc = false;
+        tc_smem = 0;
+    }
+    if (e == cudaSuccess && tc_smem) {
+        const int v = int(tc_smem);
+        e = cudaFuncSetAttribute(k_conv_tc<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, v);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_conv_tc<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, v);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_conv_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, v);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_conv_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, v);
+    }
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_conv_fwd<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(fwd_smem));
     if (e == cudaSuccess)
@@ -632,9 +846,27 @@ fwr_status fwr_net_set_weights(fwr_net* n, const float* host, int count) {
     cudaError_t e = cudaMemcpy(n->W, host, n->nparam * sizeof(float), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) {
         k_to_bf16<<<blocks(n->nparam, 256), 256>>>(n->W, int(n->nparam), n->Wb);
-        e = cudaDeviceSynchronize();
+        e = pack_weights(n, 0);
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
     }
     return e == cudaSuccess ? FWR_OK : fwr::cuda_fail(e, "fwr_net_set_weights");
+}
+
+fwr_status fwr_net_set_option(fwr_net* n, int option, int value) {
+    if (!n) return FWR_ERR_ARG;
+    if (option == FWR_NET_OPT_CONV) {
+        if (value != FWR_NET_CONV_AUTO && value != FWR_NET_CONV_SIMT) return FWR_ERR_ARG;
+        n->conv = value;
+        return FWR_OK;
+    }
+    return FWR_ERR_ARG;
+}
+
+int fwr_net_tc_layers(const fwr_net* n) {
+    if (!n) return -1;
+    int c = 0;
+    for (const Layer& L : n->layers) c += L.tc ? 1 : 0;
+    return c;
 }
 
 fwr_status fwr_net_forward(fwr_net* n, const fwr_plan* p, const float* slopes, int F, float* ext_init, void* stream) {
@@ -693,6 +925,7 @@ fwr_status fwr_net_train_step(fwr_net* n, const fwr_plan* p, const float* slopes
     k_adam<<<blocks(n->nparam, 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(
         n->W, n->G, n->M, n->V, int(n->nparam), lr, b1, b2, 1e-8f, c1, c2, n->Wb);
     cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = pack_weights(n, static_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? FWR_OK : fwr::cuda_fail(e, "fwr_net_train_step");
 }
 

@@ -2,6 +2,8 @@
 // fwr_batch.cpp). Not installed.
 #pragma once
 
+#include <vector>
+
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -28,12 +30,24 @@ void set_last_error(const char* msg);
 
 }  // namespace fwr
 
+struct fwr_plan;
+
+namespace fwr {
+// The FP32 path of plan p through the fused kernel with a BF16 warm start
+// ([F][2][N][N] bit patterns, 8-byte aligned); cudaErrorNotSupported when the
+// plan does not take the fused path (N = 256, the DFT-GEMM transform, grids
+// the fused kernel does not cover).
+cudaError_t launch_warm_bf16(fwr_plan* p, const float* slopes, const uint16_t* ext_init_h, int n_frames, int iters,
+                             float* phase, cudaStream_t s);
+}  // namespace fwr
+
 struct fwr_plan {
     int n = 0, N = 0, off = 0, filter = 0, periodic = FWR_PERIODIC_BEFORE_EACH_FFT, nvalid = 0;
     int transform = FWR_TRANSFORM_FFT;
     int device = 0;
     double noise_var = 0, r0 = 0, L0 = 0;
     uint8_t* d_mask = nullptr;
+    std::vector<uint8_t> h_mask;  // host copy of the pupil mask (0/1)
     unsigned* d_status = nullptr;
     fwr::DevTables<float> f32;
     fwr::DevTables<double> f64;

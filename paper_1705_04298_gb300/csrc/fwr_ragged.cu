@@ -38,7 +38,7 @@ ragged_kernel(RaggedParams rp) {
             cur = pl;
         }
         bool ok;
-        if (P.N == 128) ok = fused_frame<float, 128>(fc, rp.slopes[f], nullptr, rp.phase[f], nullptr, rp.iters);
+        if (P.N == 128) ok = fused_frame<float, 128>(fc, rp.slopes[f], nullptr, nullptr, rp.phase[f], nullptr, rp.iters);
         else ok = slab_frame(sc, P.tab, rp.slopes[f], nullptr, rp.phase[f], rp.iters, G);
         if (!ok) atomicOr(P.status, STATUS_NONFINITE);
         __syncthreads();

@@ -1,0 +1,318 @@
+// BF16 GEMM on the 5th-generation tensor cores (sm_103a): D = A B^T with
+// A [M][K] and B [N][K] both K-major BF16, D [M][N] row-major (FP32 or BF16),
+// FP32 accumulation in tensor memory (TMEM).
+//
+// Persistent and warp-specialised: one CTA per SM walks the 128 x BN output
+// tiles t = blockIdx.x, blockIdx.x + gridDim.x, ... (M-tile fastest, so CTAs
+// running at the same time share the B tile in L2). Six warps:
+//   warp 0, lane 0   producer: TMA loads of the A (64 x 128) and B (64 x BN)
+//                    k-blocks (64 K elements = one 128-byte swizzle row) into
+//                    a ring of STAGES shared-memory stages, across tile
+//                    boundaries; completion counted on the stage's "full"
+//                    mbarrier
+//   warp 1, lane 0   issuer: four tcgen05.mma (M 128, N BN, K 16) per k-block
+//                    into one of two TMEM accumulators (2 BN columns in all),
+//                    tcgen05.commit to the stage's "empty" mbarrier and, after
+//                    a tile's last k-block, to the accumulator's "full" barrier
+//   warps 2-5        epilogue: tcgen05.ld of their 32 accumulator lanes
+//                    (rows; warp w reads lanes 32 (w mod 4) ..), conversion,
+//                    row-wise stores, then an arrive on the accumulator's
+//                    "empty" barrier, so the next tile's MMAs run meanwhile
+// Every mbarrier wait gives up after about two seconds (clock64), sets the
+// CTA's abort flag and the caller's status word; the roles then skip their
+// work, the producer waits (bounded) for its loads in flight, the issuer for
+// its MMAs, and the TMEM is freed before the CTA returns.
+//
+// Shared-memory operand layout: the canonical K-major 128-byte-swizzle layout
+// that TMA writes with CU_TENSOR_MAP_SWIZZLE_128B for a box of 64 x rows: row
+// r at byte 128 r, its 16-byte chunk c at chunk position c ^ (r mod 8), stage
+// bases 1024-byte aligned. The matrix descriptor carries the start address,
+// an 8-row stride of 1024 bytes and the swizzle mode; the k-th 16-element
+// slice of the 64-element row is the start address plus 32 k bytes (the
+// swizzle is applied to the final address).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fwr {
+namespace umma {
+
+constexpr int BM = 128, BK = 64, THREADS = 192;
+constexpr long long WAIT_LIMIT = 4000000000LL;  // cycles (about 2 s at 2 GHz)
+
+// Per-BN configuration (BN = 128 or 256): 192 KB of stages either way
+template <int BN>
+struct Cfg {
+    static_assert(BN == 128 || BN == 256, "tile width");
+    static constexpr uint32_t A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2, STAGE_BYTES = A_BYTES + B_BYTES;
+    static constexpr int STAGES = BN == 256 ? 4 : 6;
+    static constexpr uint32_t TMEM_COLS = 2 * BN;
+    // kind::f16 instruction descriptor: FP32 accumulator, BF16 A and B, both
+    // K-major, N = BN, M = BM
+    static constexpr uint32_t IDESC =
+        (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(BN >> 3) << 17) | (uint32_t(BM >> 4) << 24);
+    // stages + 1 KB alignment slack + barriers and flags
+    static constexpr size_t SMEM = size_t(STAGES) * STAGE_BYTES + 1024 + 256;
+};
+
+__device__ __forceinline__ uint32_t su32(const void* p) { return uint32_t(__cvta_generic_to_shared(p)); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on phase `parity`; false when the CTA aborted or the limit ran out.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort) {
+    const long long t0 = clock64();
+    while (!mbar_try(bar, parity)) {
+        if (*abort) return false;
+        if (clock64() - t0 > WAIT_LIMIT) {
+            *abort = 1;
+            return false;
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+        "[%4];\n" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+// K-major, 128-byte swizzle, 8-row groups 1024 bytes apart
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+    uint64_t d = uint64_t((saddr & 0x3FFFFu) >> 4);
+    d |= uint64_t(1) << 16;            // leading-dimension offset (16 B; not used by swizzled K-major)
+    d |= uint64_t(1024 >> 4) << 32;    // stride-dimension offset
+    d |= uint64_t(1) << 46;            // descriptor version
+    d |= uint64_t(2) << 61;            // 128-byte swizzle
+    return d;
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t accum) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+            tmem),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(accum)
+        : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
+        "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+          "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+
+template <typename OutT>
+__device__ __forceinline__ void store32(OutT* dst, const uint32_t (&v)[32]);
+
+template <>
+__device__ __forceinline__ void store32<float>(float* dst, const uint32_t (&v)[32]) {
+    float4* d = reinterpret_cast<float4*>(dst);
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+        d[i] = make_float4(__uint_as_float(v[4 * i]), __uint_as_float(v[4 * i + 1]), __uint_as_float(v[4 * i + 2]),
+                           __uint_as_float(v[4 * i + 3]));
+}
+
+template <>
+__device__ __forceinline__ void store32<__nv_bfloat16>(__nv_bfloat16* dst, const uint32_t (&v)[32]) {
+    uint4* d = reinterpret_cast<uint4*>(dst);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        uint32_t w[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const __nv_bfloat162 h =
+                __floats2bfloat162_rn(__uint_as_float(v[8 * i + 2 * j]), __uint_as_float(v[8 * i + 2 * j + 1]));
+            w[j] = *reinterpret_cast<const uint32_t*>(&h);
+        }
+        d[i] = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+}
+
+// bounded wait without an abort check (draining work already issued)
+__device__ __forceinline__ void mbar_drain(uint32_t bar, uint32_t parity, volatile int* abort) {
+    const long long t0 = clock64();
+    while (!mbar_try(bar, parity))
+        if (clock64() - t0 > WAIT_LIMIT) {
+            *abort = 1;
+            return;
+        }
+}
+
+// D[M][ldd] = A B^T over K, N a multiple of BN. The maps describe A as {K, M}
+// with box {64, 128} and B as {K, N} with box {64, BN}; K beyond the tensors'
+// extent and rows beyond M read as zeros (TMA fill) and are not stored.
+template <int BN, typename OutT>
+__global__ void __launch_bounds__(THREADS, 1)
+    gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int M, int N,
+                int K, OutT* __restrict__ D, long long ldd, int* status) {
+    typedef Cfg<BN> C;
+    constexpr int S = C::STAGES;
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = su32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    uint8_t* const gbase = smem_raw + (base - raw);
+    // barriers: full[S], empty[S], acc_full[2], acc_empty[2], mma_done; then
+    // the TMEM address and the abort flag
+    uint64_t* const bars = reinterpret_cast<uint64_t*>(gbase + S * C::STAGE_BYTES);
+    uint32_t* const tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * S + 5);
+    volatile int* const abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    const uint32_t full0 = su32(bars), empty0 = full0 + 8 * S, accf0 = empty0 + 8 * S, acce0 = accf0 + 16,
+                   mma_done = acce0 + 16;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tiles_m = (M + BM - 1) / BM, tiles = tiles_m * (N / BN), kblocks = (K + BK - 1) / BK;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(full0 + 8 * s, 1);
+            mbar_init(empty0 + 8 * s, 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(accf0 + 8 * b, 1);
+            mbar_init(acce0 + 8 * b, 4);  // one arrive per epilogue warp
+        }
+        mbar_init(mma_done, 1);
+        *abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];\n" ::"l"(reinterpret_cast<uint64_t>(&mapA)) : "memory");
+        asm volatile("prefetch.tensormap [%0];\n" ::"l"(reinterpret_cast<uint64_t>(&mapB)) : "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(su32(tmem_slot)),
+                     "r"(C::TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // producer
+            int it = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+                const int m0 = (t % tiles_m) * BM, n0 = (t / tiles_m) * BN;
+                for (int kb = 0; kb < kblocks; ++kb, ++it) {
+                    const int s = it % S, use = it / S;
+                    if (use > 0 && !mbar_wait(empty0 + 8 * s, uint32_t(use - 1) & 1u, abort)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t sa = base + s * C::STAGE_BYTES, sb = sa + C::A_BYTES;
+                    mbar_expect_tx(full0 + 8 * s, C::STAGE_BYTES);
+                    tma_load_2d(sa, &mapA, kb * BK, m0, full0 + 8 * s);
+                    tma_load_2d(sb, &mapB, kb * BK, n0, full0 + 8 * s);
+                }
+            }
+            // every load issued must land before the CTA may exit
+            for (int j = it > S ? it - S : 0; j < it; ++j) mbar_drain(full0 + 8 * (j % S), uint32_t(j / S) & 1u, abort);
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // MMA issuer
+            int it = 0, jt = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++jt) {
+                const int b = jt & 1, ub = jt >> 1;
+                if (ub > 0 && !mbar_wait(acce0 + 8 * b, uint32_t(ub - 1) & 1u, abort)) break;
+                fence_after();
+                const uint32_t d = tmem + uint32_t(b * BN);
+                for (int kb = 0; kb < kblocks; ++kb, ++it) {
+                    const int s = it % S, use = it / S;
+                    if (!mbar_wait(full0 + 8 * s, uint32_t(use) & 1u, abort)) {
+                        ok = false;
+                        break;
+                    }
+                    fence_after();
+                    const uint32_t sa = base + s * C::STAGE_BYTES, sb = sa + C::A_BYTES;
+#pragma unroll
+                    for (int k = 0; k < BK / 16; ++k)
+                        mma_bf16(d, sdesc(sa + 32u * k), sdesc(sb + 32u * k), C::IDESC, (kb > 0 || k > 0) ? 1u : 0u);
+                    mma_commit(empty0 + 8 * s);
+                }
+                if (ok) mma_commit(accf0 + 8 * b);
+            }
+            // the TMEM may be freed only after every MMA issued has completed
+            mma_commit(mma_done);
+            mbar_drain(mma_done, 0u, abort);
+        }
+        __syncwarp();
+    } else {
+        // epilogue
+        const int q = warp & 3;
+        int jt = 0;
+        for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++jt) {
+            const int b = jt & 1, ub = jt >> 1;
+            const bool ok = __all_sync(0xffffffffu, mbar_wait(accf0 + 8 * b, uint32_t(ub) & 1u, abort) && !*abort);
+            if (!ok) break;
+            fence_after();
+            const int m0 = (t % tiles_m) * BM, n0 = (t / tiles_m) * BN;
+            const int row = m0 + q * 32 + lane;
+            const uint32_t tw = tmem + uint32_t(b * BN) + (uint32_t(q * 32) << 16);
+#pragma unroll 1
+            for (int c = 0; c < BN; c += 32) {
+                uint32_t v[32];
+                tmem_ld32(tw + uint32_t(c), v);
+                if (row < M) store32<OutT>(D + row * ldd + n0 + c, v);
+            }
+            fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(acce0 + 8 * b);
+        }
+    }
+    fence_before();
+    __syncthreads();
+    if (*abort && threadIdx.x == 0) atomicExch(status, 2);
+    if (warp == 0) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(C::TMEM_COLS)
+                     : "memory");
+    }
+}
+
+}  // namespace umma
+}  // namespace fwr

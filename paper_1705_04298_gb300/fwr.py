@@ -25,6 +25,9 @@ OPT_TRANSFORM = 2
 TRANSFORM_FFT = 0
 TRANSFORM_DFT_BF16X3 = 1
 STATIC_SCRATCH_GRIDS = 16
+NET_OPT_CONV = 1
+NET_CONV_AUTO = 0
+NET_CONV_SIMT = 1
 
 STATUS = {0: "FWR_OK", 1: "FWR_ERR_ARG", 2: "FWR_ERR_UNSUPPORTED", 3: "FWR_ERR_CUDA",
           4: "FWR_ERR_NONFINITE", 5: "FWR_ERR_TIMEOUT"}
@@ -63,6 +66,15 @@ SIGNATURES = {
     "fwr_net_forward": (_I, [_P, _P, _P, _I, _P, _P]),
     "fwr_net_gradients": (_I, [_P, _P, _P, _P, _I, _P, _P, _P]),
     "fwr_net_train_step": (_I, [_P, _P, _P, _P, _I, ctypes.c_float, _P, _P]),
+    "fwr_net_set_option": (_I, [_P, _I, _I]),
+    "fwr_net_tc_layers": (_I, [_P]),
+    "fwr_linws_create": (_I, [ctypes.POINTER(_P), _P, _I, _P, _P, _I]),
+    "fwr_linws_destroy": (None, [_P]),
+    "fwr_linws_valid_count": (_I, [_P]),
+    "fwr_linws_forward": (_I, [_P, _P, _I, _P, _P]),
+    "fwr_linws_reconstruct": (_I, [_P, _P, _P, _I, _I, _P, _P]),
+    "fwr_linws_status": (_I, [_P]),
+    "fwr_gemm_bf16_tc": (_I, [_P, _P, _I, _I, _I, _P, _P]),
     "fwr_get_status": (_I, [_P]),
     "fwr_status_string": (ctypes.c_char_p, [_I]),
     "fwr_last_error": (ctypes.c_char_p, []),
@@ -362,6 +374,15 @@ class Net:
                                             ctypes.byref(loss), _stream(stream)), "fwr_net_train_step")
         return float(loss.value)
 
+    def set_conv(self, mode):
+        """NET_CONV_AUTO (tensor-core forward where the layer allows it) or
+        NET_CONV_SIMT."""
+        _check(self._lib.fwr_net_set_option(self._h, NET_OPT_CONV, int(mode)), "fwr_net_set_option")
+
+    @property
+    def tc_layers(self):
+        return self._lib.fwr_net_tc_layers(self._h)
+
     def close(self):
         if getattr(self, "_h", None):
             self._lib.fwr_net_destroy(self._h)
@@ -384,6 +405,92 @@ def schedule_lpt(costs, ctas):
                                 off.ctypes.data_as(ctypes.c_void_p), order.ctypes.data_as(ctypes.c_void_p)),
            "fwr_schedule_lpt")
     return off, order[:len(c)]
+
+
+class LinearWarmStart:
+    """Rank-r linear warm start (fwr_linws_*): ext_init = (X A) V^T on the
+    tcgen05 tensor cores, X the measured slopes of the plan's valid cells
+    (x slopes, then y slopes, row-major cell order). A: (2 n_valid, r), V:
+    (2 N^2, r), float arrays, r a multiple of 128."""
+
+    def __init__(self, plan, A, V, max_batch):
+        lib = load()
+        self._lib = lib
+        A = np.ascontiguousarray(np.asarray(A, dtype=np.float32))
+        V = np.ascontiguousarray(np.asarray(V, dtype=np.float32))
+        if A.ndim != 2 or V.ndim != 2 or A.shape[1] != V.shape[1]:
+            raise ValueError("A (2 n_valid, r) and V (2 N^2, r) must share r")
+        if A.shape[0] != 2 * plan.valid_count or V.shape[0] != 2 * plan.N * plan.N:
+            raise ValueError("A must have 2 n_valid rows and V 2 N^2 rows")
+        h = ctypes.c_void_p()
+        _check(lib.fwr_linws_create(ctypes.byref(h), plan._h, int(A.shape[1]), A.ctypes.data_as(_P),
+                                    V.ctypes.data_as(_P), int(max_batch)), "fwr_linws_create")
+        self._h = h
+        self.plan = plan
+        self.rank = int(A.shape[1])
+        self.max_batch = int(max_batch)
+
+    def forward(self, slopes, ext_init=None, stream=None):
+        """slopes (F, 2, n, n) float32 CUDA -> ext_init (F, 2, N, N) float32."""
+        import torch
+        F = slopes.shape[0]
+        _need(slopes, torch.float32, (F, 2, self.plan.n, self.plan.n), "slopes")
+        if ext_init is None:
+            ext_init = torch.empty((F, 2, self.plan.N, self.plan.N), dtype=torch.float32, device=slopes.device)
+        _need(ext_init, torch.float32, (F, 2, self.plan.N, self.plan.N), "ext_init")
+        _check(self._lib.fwr_linws_forward(self._h, _ptr(slopes), F, _ptr(ext_init), _stream(stream)),
+               "fwr_linws_forward")
+        return ext_init
+
+    def reconstruct(self, slopes, iters, phase=None, plan=None, stream=None):
+        """Warm start + `iters` Gerchberg iterations + final filter
+        (fwr_linws_reconstruct), the warm start kept in BF16. plan: the one
+        given at creation unless another with the same pupil and grid."""
+        import torch
+        plan = self.plan if plan is None else plan
+        F = slopes.shape[0]
+        _need(slopes, torch.float32, (F, 2, plan.n, plan.n), "slopes")
+        if phase is None:
+            phase = torch.empty((F, plan.N, plan.N), dtype=torch.float32, device=slopes.device)
+        _need(phase, torch.float32, (F, plan.N, plan.N), "phase")
+        _check(self._lib.fwr_linws_reconstruct(self._h, plan._h, _ptr(slopes), F, int(iters), _ptr(phase),
+                                               _stream(stream)), "fwr_linws_reconstruct")
+        return phase
+
+    def status(self):
+        _check(self._lib.fwr_linws_status(self._h), "fwr_linws_status")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.fwr_linws_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def gemm_bf16_tc(A, B, out=None, stream=None):
+    """D = A B^T (fwr_gemm_bf16_tc): A (M, K), B (N, K) bfloat16 CUDA tensors,
+    K a multiple of 8, N of 128; D float32 (M, N)."""
+    import torch
+    if A.dtype != torch.bfloat16 or B.dtype != torch.bfloat16 or A.dim() != 2 or B.dim() != 2:
+        raise ValueError("A and B must be 2-D bfloat16 tensors")
+    if A.shape[1] != B.shape[1] or not A.is_cuda or not B.is_cuda:
+        raise ValueError("A (M, K) and B (N, K) must be CUDA tensors with the same K")
+    A = A.contiguous()
+    B = B.contiguous()
+    M, K = A.shape
+    N = B.shape[0]
+    if out is None:
+        out = torch.empty((M, N), dtype=torch.float32, device=A.device)
+    _need(out, torch.float32, (M, N), "out")
+    lib = load()
+    _check(lib.fwr_gemm_bf16_tc(_ptr(A), _ptr(B), int(M), int(N), int(K), _ptr(out), _stream(stream)),
+           "fwr_gemm_bf16_tc")
+    return out
 
 
 def dft2_bf16x3(x, inverse=False, out=None, stream=None):

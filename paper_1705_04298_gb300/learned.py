@@ -31,6 +31,8 @@ TRAIN_SEED0, EVAL_SEED0 = 1_000_000, 2_000_000
 TRAIN_SIGMAS = (0.02, 0.05, 0.1)
 EVAL_SIGMA = 0.05
 TARGET_ITERS = 10
+PLAIN_ITERS = (1, 2, 3, 4, 5, 6, 8, 10)
+LEARNED_ITERS = (1, 2, 3)
 WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights", "warmstart_w16_n40.npz")
 
 
@@ -160,18 +162,24 @@ def evaluate(fwr, net, n_frames=1000, reps=20, log=print):
         return e0.elapsed_time(e1) / reps
 
     out = {}
-    for k in (1, 2, 10):
+    for k in PLAIN_ITERS:
         ms = timed(lambda: plan.reconstruct(slopes, k, phase))
         out["plain_k%d" % k] = {"residual_rad": residual_rms(fwr, phase, truth, mask), "ms": ms,
                                 "frames_per_s": n_frames / ms * 1e3}
     ms_net = timed(lambda: net.forward(plan, slopes, warm))
-    for k in (1, 2):
+    for k in LEARNED_ITERS:
         def run():
             net.forward(plan, slopes, warm)
             plan.reconstruct(slopes, k, phase, ext_init=warm)
         ms = timed(run)
-        out["learned_k%d" % k] = {"residual_rad": residual_rms(fwr, phase, truth, mask), "ms": ms,
-                                  "net_ms": ms_net, "frames_per_s": n_frames / ms * 1e3}
+        r = residual_rms(fwr, phase, truth, mask)
+        # the cheapest plain loop that reaches at least this residual
+        match = [j for j in PLAIN_ITERS if out["plain_k%d" % j]["residual_rad"] <= r]
+        ref = out["plain_k%d" % match[0]] if match else None
+        out["learned_k%d" % k] = {"residual_rad": r, "ms": ms, "net_ms": ms_net,
+                                  "frames_per_s": n_frames / ms * 1e3,
+                                  "plain_iters_same_residual": match[0] if match else None,
+                                  "speedup_same_residual": ref["ms"] / ms if ref else None}
     for key, v in out.items():
         log("%-11s residual %.4f rad  %.3f ms  %.0f frames/s" % (key, v["residual_rad"], v["ms"], v["frames_per_s"]))
     return out

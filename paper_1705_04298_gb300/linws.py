@@ -1,0 +1,175 @@
+"""Linear warm start: the extension operator of the Gerchberg loop, its
+data-weighted rank-r truncation, and the evaluation driver.
+
+Algorithm 1 (Sec. 3.3) is linear in the measured slopes: from a zero start,
+the extended slopes after k iterations are E_k s for a fixed matrix E_k that
+depends only on the pupil, the grid and the periodic mode. Its rows are the
+loop's responses to unit slopes, taken here from the library's own FP32 path
+(fwr_reconstruct_ex with ext_out), one frame per valid slope.
+
+A warm start x0 = E_k s followed by one more iteration reproduces k + 1 plain
+iterations. E_10 is 2 n_valid x 2 N^2 (2528 x 32768 for 40 x 40 lenslets on a
+128^2 grid): 166 MFLOP per frame, which the tcgen05 tensor cores evaluate far
+faster than the nine FP32 FFT iterations it replaces. A rank-r factorisation
+E ~ A V^T cuts that further. It is fitted to data (reduced-rank regression):
+V holds the leading right singular vectors of X E over training frames X, so
+the truncation keeps what turbulence-like slopes excite. The fit is off-line
+host work in FP64 (numpy); inference runs entirely in the library
+(fwr_linws_forward, then fwr_reconstruct_ex).
+
+    python -m paper_1705_04298_gb300.linws eval --rank 1280
+"""
+
+import argparse
+import json
+import sys
+import time
+
+import numpy as np
+
+from . import learned
+
+TRAIN_FRAMES = 4096
+OPERATOR_ITERS = 10
+DEFAULT_RANK = 1280
+
+
+def valid_cells(mask):
+    return np.flatnonzero(np.asarray(mask, dtype=bool).ravel())
+
+
+def gathered(slopes, mask):
+    """(F, 2, n, n) slopes -> X (F, 2 n_valid): x slopes of the valid cells
+    (row-major), then y slopes."""
+    s = np.asarray(slopes)
+    cells = valid_cells(mask)
+    F = s.shape[0]
+    flat = s.reshape(F, 2, -1)
+    return np.concatenate([flat[:, 0, cells], flat[:, 1, cells]], axis=1)
+
+
+def extension_operator(fwr, plan, mask, iters=OPERATOR_ITERS, chunk=1024):
+    """E (2 n_valid, 2 N^2) float64: row j is the extension after `iters`
+    iterations for the unit slope vector e_j (library FP32 path)."""
+    import torch
+    cells = valid_cells(mask)
+    nv = len(cells)
+    K = 2 * nv
+    n, N = plan.n, plan.N
+    E = np.empty((K, 2 * N * N), dtype=np.float64)
+    for a in range(0, K, chunk):
+        b = min(K, a + chunk)
+        imp = torch.zeros((b - a, 2, n * n), dtype=torch.float32, device="cuda")
+        rows = torch.arange(b - a, device="cuda")
+        j = torch.arange(a, b, device="cuda")
+        ch = (j >= nv).long()
+        cell = torch.tensor(cells, device="cuda")[j - ch * nv]
+        imp[rows, ch, cell] = 1.0
+        ext = torch.empty((b - a, 2, N, N), dtype=torch.float32, device="cuda")
+        plan.reconstruct(imp.view(b - a, 2, n, n), iters, ext_out=ext)
+        E[a:b] = ext.reshape(b - a, -1).double().cpu().numpy()
+    return E
+
+
+def fit(E, X, rank):
+    """Reduced-rank factors (A, V) with E ~ A V^T minimising ||X E - X A V^T||_F:
+    with X = Q R, V = the leading right singular vectors of R E, A = E V.
+    rank: columns of A and V (the device wants a multiple of 128); columns
+    beyond the rank of R E are zero."""
+    r = int(rank)
+    R = np.linalg.qr(np.asarray(X, dtype=np.float64), mode="r")
+    KE = R @ E                                   # (min(F, K), 2N^2)
+    lam, U = np.linalg.eigh(KE @ KE.T)           # ascending
+    keep = min(r, KE.shape[0])
+    lam = lam[::-1][:keep]
+    U = U[:, ::-1][:, :keep]
+    cols = np.flatnonzero(lam > lam[0] * 1e-20)
+    V = np.zeros((E.shape[1], r))
+    V[:, cols] = (KE.T @ U[:, cols]) / np.sqrt(lam[cols])
+    A = E @ V
+    return A.astype(np.float32), V.astype(np.float32)
+
+
+def build(fwr, plan, mask, rank=DEFAULT_RANK, max_batch=1000, frames=TRAIN_FRAMES, iters=OPERATOR_ITERS,
+          log=None):
+    """Operator from the library, training slopes from the seeded generator
+    (seeds 1e6 + i, noise cycling 0.02, 0.05, 0.1 rad), fit, device object."""
+    from . import synth
+    t0 = time.time()
+    E = extension_operator(fwr, plan, mask, iters)
+    t1 = time.time()
+    sl, _, _ = synth.batch(plan.n, frames, learned.TRAIN_SEED0, list(learned.TRAIN_SIGMAS), learned.R0, learned.L0)
+    X = gathered(sl, mask)
+    t2 = time.time()
+    A, V = fit(E, X, rank)
+    t3 = time.time()
+    if log:
+        log("operator %.1f s, training slopes %.1f s, fit %.1f s" % (t1 - t0, t2 - t1, t3 - t2))
+    return fwr.LinearWarmStart(plan, A, V, max_batch), E
+
+
+def evaluate(fwr, rank=DEFAULT_RANK, n_frames=1000, reps=20, log=print):
+    """Residual and frames/s of the plain loop against the linear warm start
+    followed by k = 1, 2 iterations, on the evaluation frames of the learned
+    warm start (40 x 40 lenslets, 128^2 grid, 0.05 rad noise, Wiener)."""
+    import torch
+    from . import synth
+    mask = synth.pupil_mask(learned.N_LENSLETS)
+    plan = learned.make_plan(fwr, fwr.WIENER, learned.EVAL_SIGMA)
+    ws, _ = build(fwr, plan, mask, rank, max_batch=n_frames, log=log)
+    slopes, truth = learned.frames(n_frames, learned.EVAL_SEED0, learned.EVAL_SIGMA)
+    phase = torch.empty((n_frames, learned.GRID, learned.GRID), device="cuda")
+    warm = torch.empty((n_frames, 2, learned.GRID, learned.GRID), device="cuda")
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    out = {}
+    for k in learned.PLAIN_ITERS:
+        ms = timed(lambda: plan.reconstruct(slopes, k, phase))
+        out["plain_k%d" % k] = {"residual_rad": learned.residual_rms(fwr, phase, truth, mask), "ms": ms,
+                                "frames_per_s": n_frames / ms * 1e3}
+    ms_ws = timed(lambda: ws.forward(slopes, warm))
+    ws.status()
+    for k in (1, 2):
+        def run():
+            ws.forward(slopes, warm)
+            plan.reconstruct(slopes, k, phase, ext_init=warm)
+        ms = timed(run)
+        r = learned.residual_rms(fwr, phase, truth, mask)
+        p10 = out["plain_k10"]
+        out["linear_r%d_k%d" % (rank, k)] = {
+            "residual_rad": r, "ms": ms, "warm_start_ms": ms_ws, "frames_per_s": n_frames / ms * 1e3,
+            "residual_vs_plain_k10": r / p10["residual_rad"], "speedup_vs_plain_k10": p10["ms"] / ms}
+    ws.status()
+    for key, v in out.items():
+        log("%-16s residual %.4f rad  %.3f ms  %.0f frames/s" % (key, v["residual_rad"], v["ms"],
+                                                                  v["frames_per_s"]))
+    return out
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("cmd", choices=["eval"])
+    ap.add_argument("--rank", type=int, default=DEFAULT_RANK)
+    ap.add_argument("--frames", type=int, default=1000)
+    args = ap.parse_args(argv)
+    from . import fwr
+    fwr.load()
+    res = evaluate(fwr, args.rank, args.frames)
+    print(json.dumps(res))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -61,8 +61,8 @@ def oracle_run(params, w, sl, mask, off, ext):
     return out, loss, g
 
 
-def test_gradients_match_reference(fwr):
-    w, F = 4, 3
+@pytest.mark.parametrize("w,F", [(4, 3), (16, 2)])
+def test_gradients_match_reference(fwr, w, F):
     plan, sl, mask, off, ext, params = setup_problem(fwr, w, F, 21)
     net = fwr.Net(w, F, params)
     assert net.param_count == unet.param_count(w)
@@ -84,16 +84,42 @@ def test_gradients_match_reference(fwr):
         assert c >= 0.99, (name, c)
 
 
-def test_forward_matches_reference(fwr):
-    w, F = 4, 2
+@pytest.mark.parametrize("w,F", [(4, 2), (8, 3), (16, 5)])
+def test_forward_matches_reference(fwr, w, F):
+    """w = 4 and 8: a mix of CUDA-core and tensor-core convolutions (the
+    levels with 16k channels go to the tensor cores); w = 16: all 3 x 3
+    convolutions but the first. F = 5 at w = 16 leaves ragged CTA tiles at
+    the 4 x 4 level (80 pixels)."""
     plan, sl, mask, off, ext, params = setup_problem(fwr, w, F, 5)
     net = fwr.Net(w, F, params)
+    assert net.tc_layers == {4: 5, 8: 9, 16: 13}[w]
     s = torch.tensor(sl, dtype=torch.float32, device="cuda")
     ws = net.forward(plan, s).cpu().numpy().astype(np.float64)
     out_o, _, _ = oracle_run(params, w, sl, mask, off, ext)
     for f in range(F):
         ref = unet.warm_start(out_o[f])
         assert np.linalg.norm(ws[f] - ref) <= 2e-2 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("w,F", [(16, 7), (32, 2)])
+def test_tensor_core_forward_matches_simt(fwr, w, F):
+    """Same weights and inputs, tensor-core and CUDA-core convolutions: both
+    sum in FP32 and differ only in order, so the predictions agree to a few
+    BF16 roundings of the activations."""
+    plan, sl, mask, off, ext, params = setup_problem(fwr, w, F, 9)
+    net = fwr.Net(w, F, params)
+    assert net.tc_layers == 13
+    s = torch.tensor(sl, dtype=torch.float32, device="cuda")
+    a = net.forward(plan, s).clone()
+    net.set_conv(fwr.NET_CONV_SIMT)
+    b = net.forward(plan, s).clone()
+    net.set_conv(fwr.NET_CONV_AUTO)
+    c = net.forward(plan, s)
+    assert torch.equal(a, c)
+    rel = float((a - b).norm() / b.norm())
+    assert rel <= 1e-2, rel
+    with pytest.raises(RuntimeError):
+        net.set_conv(7)
 
 
 def test_training_lowers_the_loss(fwr):
