@@ -199,7 +199,8 @@ def extra_measurements(fwr, synth, torch, flush):
     flushed): 40x40 at each iteration count, the 16x16 single-frame latency
     (FP32 and FP64), a ragged 4096-frame batch of 40/64/80/128-lenslet pupils
     (one graph-captured launch, autotuned schedule) and 128x128 lenslets on a
-    256^2 grid with 10 iterations."""
+    256^2 grid with 10 iterations. The warm starts are measured by
+    learned_measurements."""
     peak = fp32_peak_tflops()
     res = {}
     # 40x40 on 128^2, k in {0, 1, 2, 5}
@@ -275,6 +276,73 @@ def extra_measurements(fwr, synth, torch, flush):
     tf = flops_per_frame(256, 10) * 1000 / (ms / 1e3) / 1e12
     res["128x128_256grid_k10_frozen_flow"] = {"frames_per_s": 1000 / (ms / 1e3), "ms": ms, "tflops": tf,
                                               "frac": tf / peak}
+    return res
+
+
+def measured_bf16_peak():
+    """Dense BF16 tensor peak (TFLOP/s): the measured cuBLAS burst
+    figure when MEASURED_PEAKS.json is present, else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["bf16_tflops"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 1900.0, "fallback"
+
+
+def learned_measurements(fwr, torch, flush):
+    """Warm starts against the plain loop on the held-out frames of the
+    warm-start workload (40x40 on 128^2, sigma 0.05 rad, Wiener, 1000
+    frames, seeds 2e6 + i): residual phase rms against the true screens and
+    frames/s (device time, L2 flushed) of the plain loop at k = 1..10, of the
+    U-Net (committed weights) followed by k = 1, 2, and of the rank-1280
+    linear warm start followed by k = 1, 2 (fwr_linws_reconstruct); the
+    equal-residual comparison; the warm start's tensor roofline."""
+    from paper_1705_04298_gb300 import learned, linws, synth
+    F = 1000
+    mask = synth.pupil_mask(learned.N_LENSLETS)
+    plan = learned.make_plan(fwr, fwr.WIENER, learned.EVAL_SIGMA)
+    slopes, truth = learned.frames(F, learned.EVAL_SEED0, learned.EVAL_SIGMA)
+    phase = torch.empty((F, 128, 128), device="cuda")
+    warm = torch.empty((F, 2, 128, 128), device="cuda")
+
+    def entry(fn, reps=20):
+        for _ in range(3):
+            fn()
+        ms = _time_launches(fn, flush, reps, torch)
+        return {"residual_rad": learned.residual_rms(fwr, phase, truth, mask), "ms": ms,
+                "frames_per_s": F / (ms / 1e3)}
+
+    res = {"plain": {}, "unet": {}, "linear_r1280": {}}
+    for k in (1, 2, 3, 4, 5, 6, 8, 10):
+        res["plain"]["k%d" % k] = entry(lambda: plan.reconstruct(slopes, k, phase))
+    net = learned.load_net(fwr, learned.WEIGHTS, max_batch=F)
+    for k in (1, 2):
+        res["unet"]["k%d" % k] = entry(lambda: (net.forward(plan, slopes, warm),
+                                                plan.reconstruct(slopes, k, phase, ext_init=warm)))
+    ws, _ = linws.build(fwr, plan, mask, 1280, max_batch=F)
+    for k in (1, 2):
+        res["linear_r1280"]["k%d" % k] = entry(lambda: ws.reconstruct(slopes, k, phase))
+    ws.status()
+    p10 = res["plain"]["k10"]
+    for fam in ("unet", "linear_r1280"):
+        for k, v in res[fam].items():
+            # the cheapest plain loop reaching this residual, and the target
+            # comparison: against ten plain iterations
+            match = [kk for kk, pv in res["plain"].items() if pv["residual_rad"] <= v["residual_rad"]]
+            v["plain_k_same_residual"] = match[0] if match else None
+            v["speedup_same_residual"] = (res["plain"][match[0]]["ms"] / v["ms"]) if match else None
+            v["residual_vs_plain_k10"] = v["residual_rad"] / p10["residual_rad"]
+            v["speedup_vs_plain_k10"] = p10["ms"] / v["ms"]
+    # the warm start alone (gather + two tcgen05 GEMMs), FP32 output
+    ms_ws = _time_launches(lambda: ws.forward(slopes, warm), flush, 20, torch)
+    ws.status()
+    K = 2 * plan.valid_count
+    fl = 2.0 * F * 1280 * (K + 2 * 128 * 128)
+    peak, src = measured_bf16_peak()
+    res["linear_r1280"]["warm_start_roofline"] = {
+        "bound": "tensor", "achieved": fl / (ms_ws / 1e3) / 1e12, "peak": peak, "peak_source": src,
+        "unit": "TFLOP/s", "frac": fl / (ms_ws / 1e3) / 1e12 / peak, "ms": ms_ws, "flops_per_launch": fl,
+        "kernels": "k_gather + umma::gemm_kernel (X A, then (X A) V^T)"}
     return res
 
 
@@ -414,6 +482,7 @@ def main():
     extras = None
     if rank == 0 and not args.no_extras:
         extras = extra_measurements(fwr, synth, torch, flush)
+        extras["learned_warm_start_40x40_128grid"] = learned_measurements(fwr, torch, flush)
 
     if rank == 0:
         fl = flops_per_frame(N, k) * FRAMES

@@ -18,6 +18,7 @@ host work in FP64 (numpy); inference runs entirely in the library
 (fwr_linws_forward, then fwr_reconstruct_ex).
 
     python -m paper_1705_04298_gb300.linws eval --rank 1280
+    python -m paper_1705_04298_gb300.linws time --rank 1280 --reps 20
 """
 
 import argparse
@@ -158,14 +159,50 @@ def evaluate(fwr, rank=DEFAULT_RANK, n_frames=1000, reps=20, log=print):
     return out
 
 
+def time_warm_start(fwr, rank=DEFAULT_RANK, n_frames=1000, reps=20, iters=1, log=print):
+    """Device time (CUDA events, mean of reps) of the warm start alone
+    (fwr_linws_forward: gather and the two tcgen05 GEMMs) and of the whole
+    fwr_linws_reconstruct call, on the evaluation frames."""
+    import torch
+    from . import synth
+    mask = synth.pupil_mask(learned.N_LENSLETS)
+    plan = learned.make_plan(fwr, fwr.WIENER, learned.EVAL_SIGMA)
+    ws, _ = build(fwr, plan, mask, rank, max_batch=n_frames, frames=1024)
+    slopes, _ = learned.frames(n_frames, learned.EVAL_SEED0, learned.EVAL_SIGMA)
+    warm = torch.empty((n_frames, 2, learned.GRID, learned.GRID), device="cuda")
+    phase = torch.empty((n_frames, learned.GRID, learned.GRID), device="cuda")
+    out = {}
+    for name, fn in (("warm_start", lambda: ws.forward(slopes, warm)),
+                     ("reconstruct_k%d" % iters, lambda: ws.reconstruct(slopes, iters, phase))):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        out[name + "_ms"] = e0.elapsed_time(e1) / reps
+    ws.status()
+    log(json.dumps(out))
+    return out
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("cmd", choices=["eval"])
+    ap.add_argument("cmd", choices=["eval", "time"])
     ap.add_argument("--rank", type=int, default=DEFAULT_RANK)
     ap.add_argument("--frames", type=int, default=1000)
+    ap.add_argument("--reps", type=int, default=20)
+    ap.add_argument("--iters", type=int, default=1)
     args = ap.parse_args(argv)
     from . import fwr
     fwr.load()
+    if args.cmd == "time":
+        time_warm_start(fwr, args.rank, args.frames, args.reps, args.iters)
+        return 0
     res = evaluate(fwr, args.rank, args.frames)
     print(json.dumps(res))
     return 0
