@@ -294,11 +294,14 @@ def learned_measurements(fwr, torch, flush):
     warm-start workload (40x40 on 128^2, sigma 0.05 rad, Wiener, 1000
     frames, seeds 2e6 + i): residual phase rms against the true screens and
     frames/s (device time, L2 flushed) of the plain loop at k = 1..10, of the
-    U-Net (committed weights) followed by k = 1, 2, and of the rank-1280
-    linear warm start followed by k = 1, 2 (fwr_linws_reconstruct); the
+    U-Net (committed weights) followed by k = 1, 2, and of the linear warm
+    start (rank linws.DEFAULT_RANK) followed by k = 1, 2 through
+    fwr_linws_reconstruct, called directly and replayed from a CUDA graph
+    (its four kernels are short: the graph removes the host launch gaps); the
     equal-residual comparison; the warm start's tensor roofline."""
     from paper_1705_04298_gb300 import learned, linws, synth
     F = 1000
+    rank = linws.DEFAULT_RANK
     mask = synth.pupil_mask(learned.N_LENSLETS)
     plan = learned.make_plan(fwr, fwr.WIENER, learned.EVAL_SIGMA)
     slopes, truth = learned.frames(F, learned.EVAL_SEED0, learned.EVAL_SIGMA)
@@ -312,19 +315,30 @@ def learned_measurements(fwr, torch, flush):
         return {"residual_rad": learned.residual_rms(fwr, phase, truth, mask), "ms": ms,
                 "frames_per_s": F / (ms / 1e3)}
 
-    res = {"plain": {}, "unet": {}, "linear_r1280": {}}
+    lin = "linear_r%d" % rank
+    res = {"plain": {}, "unet": {}, lin: {}}
     for k in (1, 2, 3, 4, 5, 6, 8, 10):
         res["plain"]["k%d" % k] = entry(lambda: plan.reconstruct(slopes, k, phase))
     net = learned.load_net(fwr, learned.WEIGHTS, max_batch=F)
     for k in (1, 2):
         res["unet"]["k%d" % k] = entry(lambda: (net.forward(plan, slopes, warm),
                                                 plan.reconstruct(slopes, k, phase, ext_init=warm)))
-    ws, _ = linws.build(fwr, plan, mask, 1280, max_batch=F)
+    ws, _ = linws.build(fwr, plan, mask, rank, max_batch=F)
     for k in (1, 2):
-        res["linear_r1280"]["k%d" % k] = entry(lambda: ws.reconstruct(slopes, k, phase))
+        v = entry(lambda: ws.reconstruct(slopes, k, phase))
+        stream = torch.cuda.Stream()
+        stream.wait_stream(torch.cuda.current_stream())
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=stream):
+            ws.reconstruct(slopes, k, phase, stream=stream)
+        torch.cuda.synchronize()
+        g = entry(graph.replay)
+        v["graph_ms"] = g["ms"]
+        v["graph_frames_per_s"] = g["frames_per_s"]
+        res[lin]["k%d" % k] = v
     ws.status()
     p10 = res["plain"]["k10"]
-    for fam in ("unet", "linear_r1280"):
+    for fam in ("unet", lin):
         for k, v in res[fam].items():
             # the cheapest plain loop reaching this residual, and the target
             # comparison: against ten plain iterations
@@ -333,13 +347,15 @@ def learned_measurements(fwr, torch, flush):
             v["speedup_same_residual"] = (res["plain"][match[0]]["ms"] / v["ms"]) if match else None
             v["residual_vs_plain_k10"] = v["residual_rad"] / p10["residual_rad"]
             v["speedup_vs_plain_k10"] = p10["ms"] / v["ms"]
+            if "graph_ms" in v:
+                v["graph_speedup_vs_plain_k10"] = p10["ms"] / v["graph_ms"]
     # the warm start alone (gather + two tcgen05 GEMMs), FP32 output
     ms_ws = _time_launches(lambda: ws.forward(slopes, warm), flush, 20, torch)
     ws.status()
     K = 2 * plan.valid_count
-    fl = 2.0 * F * 1280 * (K + 2 * 128 * 128)
+    fl = 2.0 * F * rank * (K + 2 * 128 * 128)
     peak, src = measured_bf16_peak()
-    res["linear_r1280"]["warm_start_roofline"] = {
+    res[lin]["warm_start_roofline"] = {
         "bound": "tensor", "achieved": fl / (ms_ws / 1e3) / 1e12, "peak": peak, "peak_source": src,
         "unit": "TFLOP/s", "frac": fl / (ms_ws / 1e3) / 1e12 / peak, "ms": ms_ws, "flops_per_launch": fl,
         "kernels": "k_gather + umma::gemm_kernel (X A, then (X A) V^T)"}

@@ -128,7 +128,9 @@ fwr_status fwr_plan_set_option(fwr_plan* plan, int key, double value);
  *               outside the mask are ignored
  *   iters       Gerchberg iterations, 0 <= iters <= 64 (0 = zero padding,
  *               plus the periodic fill where the option asks for it)
- *   phase_dev   [n_frames][N][N] float output, radians, zero mean
+ *   phase_dev   [n_frames][N][N] float output, radians, zero mean; 16-byte
+ *               aligned (FWR_ERR_ARG otherwise; all entry points that write
+ *               a phase)
  * n_frames = 0 is a no-op. All work is one persistent kernel launch. For
  * N = 256 the grid of each frame is streamed through shared memory from a
  * plan-owned global scratch area (one 512 KB area per SM, allocated by

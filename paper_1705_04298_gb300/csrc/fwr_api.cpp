@@ -287,6 +287,8 @@ static fwr_status check_call(const fwr_plan* p, const void* slopes, int n_frames
     if (!p || n_frames < 0 || iters < 0 || iters > 64) return FWR_ERR_ARG;
     if (n_frames > 0 && !slopes) return FWR_ERR_ARG;
     if (n_frames > 0 && !phase && !ext_out) return FWR_ERR_ARG;
+    // the phase leaves the kernels in 8- and 16-byte vector stores
+    if ((reinterpret_cast<uintptr_t>(phase) & 15u) != 0) return FWR_ERR_ARG;
     return FWR_OK;
 }
 

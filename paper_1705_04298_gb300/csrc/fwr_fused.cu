@@ -18,7 +18,7 @@ fused_kernel(Params<T> p) {
     __shared__ int s_bad;
     if (threadIdx.x == 0) s_bad = 0;
     FusedCtx<T, N> c;
-    fused_setup<T, N>(c, smem, p.tab, p.mask, p.n, p.off, p.periodic);
+    fused_setup<T, N>(c, smem, p.tab, p.mask, p.n, p.off, p.periodic, p.wf_smem != 0);
     const int nn = p.n * p.n;
     bool finite = true;
     for (int f = blockIdx.x; f < p.F; f += gridDim.x) {
@@ -128,8 +128,11 @@ cudaError_t launch_fft2_n(const float2* in, float2* out, int F, int inverse, con
 }
 
 template <typename T, int N>
-cudaError_t launch_n(const Params<T>& p, cudaStream_t s) {
-    const size_t smem = Layout<T, N>::bytes(p.n);
+cudaError_t launch_n(const Params<T>& p0, cudaStream_t s) {
+    // keep the final-filter table in shared memory when it still fits
+    Params<T> p = p0;
+    p.wf_smem = Layout<T, N>::bytes_wf(p.n) <= size_t(227) * 1024 ? 1 : 0;
+    const size_t smem = p.wf_smem ? Layout<T, N>::bytes_wf(p.n) : Layout<T, N>::bytes(p.n);
     auto kern = fused_kernel<T, N>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;

@@ -68,7 +68,10 @@ struct Layout {
     static constexpr size_t pt = t + size_t(N) * sizeof(V);
     static constexpr size_t iota = pt + size_t(4 * N) * sizeof(T);
     static constexpr size_t s0 = (iota + size_t(H + 1) * N * sizeof(T) + 15) & ~size_t(15);
-    static size_t bytes(int n) { return s0 + size_t(n) * s0_stride(n) * sizeof(V); }
+    __host__ __device__ static size_t bytes(int n) { return s0 + size_t(n) * s0_stride(n) * sizeof(V); }
+    // optional resident copy of the final-filter half-table (same order as iota), after s0
+    __host__ __device__ static size_t wf(int n) { return (bytes(n) + 15) & ~size_t(15); }
+    __host__ __device__ static size_t bytes_wf(int n) { return wf(n) + size_t(H + 1) * N * sizeof(T); }
 };
 
 __device__ __forceinline__ void store4(float* d, float a, float b, float c, float e) {
@@ -232,7 +235,7 @@ struct FusedCtx {
 // Called by every thread of the CTA; ends with a barrier.
 template <typename T, int N>
 __device__ __forceinline__ void fused_setup(FusedCtx<T, N>& c, unsigned char* smem, const Tables<T>& tab,
-                                            const uint8_t* mask, int n, int off, int mode) {
+                                            const uint8_t* mask, int n, int off, int mode, bool wf_smem = false) {
     typedef typename cvec<T>::type V;
     typedef Layout<T, N> L;
     constexpr int R = N / 4, NT = 4 * N, H = N / 2, S = L::S;
@@ -246,6 +249,7 @@ __device__ __forceinline__ void fused_setup(FusedCtx<T, N>& c, unsigned char* sm
     T* pt = c.pt = reinterpret_cast<T*>(smem + L::pt);
     T* iota = c.iota = reinterpret_cast<T*>(smem + L::iota);
     V* s0 = c.s0 = reinterpret_cast<V*>(smem + L::s0);
+    T* const wf = wf_smem ? reinterpret_cast<T*>(smem + L::wf(n)) : nullptr;
     c.mask = mask;
     c.n = n;
     c.off = off;
@@ -263,8 +267,9 @@ __device__ __forceinline__ void fused_setup(FusedCtx<T, N>& c, unsigned char* sm
     // 1/|G|^2 weights in storage-column order (entry [ky][col] holds kx(col)),
     // so the lanes of a warp read consecutive words
     for (int i = tid; i < (H + 1) * N; i += NT) {
-        const int col = i % N;
-        iota[i] = tab.iota[(i / N) * N + (col >> 2) + R * (col & 3)];
+        const int col = i % N, src = (i / N) * N + (col >> 2) + R * (col & 3);
+        iota[i] = tab.iota[src];
+        if (wf) wf[i] = tab.wfin[src];
     }
     __syncthreads();
     for (int i = tid; i < 4 * R; i += NT) tw1[i] = tw[(i & 3) * (i >> 2)];
@@ -316,8 +321,9 @@ __device__ __forceinline__ void fused_setup(FusedCtx<T, N>& c, unsigned char* sm
     c.twv = tw + q1;                  // twv[4 q2] = tw[ky]
     c.iop = iota + q1 * N + gam;       // iop[4 N q2] = 1/|G|^2 at (ky, kx)
     c.ion = iota + (N - q1) * N + gamp; // ion[-4 N q2] = 1/|G|^2 at (-ky, -kx)
-    c.wfp = tab.wfin + q1 * N + kx;
-    c.wfn = tab.wfin + (N - q1) * N + kxn;
+    // final weights: the resident copy (storage-column order) or the table in global memory
+    c.wfp = wf ? wf + q1 * N + gam : tab.wfin + q1 * N + kx;
+    c.wfn = wf ? wf + (N - q1) * N + gamp : tab.wfin + (N - q1) * N + kxn;
     __syncthreads();
 
 }
@@ -372,11 +378,11 @@ __device__ __forceinline__ bool fused_frame(const FusedCtx<T, N>& c, const T* sl
                 load_row4(exth + rr * N + cc, ex);
                 load_row4(exth + N * N + rr * N + cc, ey);
             }
-            V* const zp = Z + rr * S + cc;
-            zp[0] = mk(ex[0], ey[0]);
-            zp[1] = mk(ex[1], ey[1]);
-            zp[2] = mk(ex[2], ey[2]);
-            zp[3] = mk(ex[3], ey[3]);
+            // two 16-byte stores per four cells (single cells at a 32-byte lane
+            // stride would conflict eight ways)
+            T* const zp = reinterpret_cast<T*>(Z + rr * S + cc);
+            store4(zp, ex[0], ey[0], ex[1], ey[1]);
+            store4(zp + 4, ex[2], ey[2], ex[3], ey[3]);
         }
     }
     for (int c = tid; c < nn; c += NT) {
@@ -528,14 +534,20 @@ __device__ __forceinline__ bool fused_frame(const FusedCtx<T, N>& c, const T* sl
             for (int n1 = 0; n1 < R; ++n1)
                 if (pmask & (1u << n1)) x[n1] = s0row[4 * n1];
         } else {
-            // real phase out, through shared memory for coalesced stores
-#pragma unroll
-            for (int n1 = 0; n1 < R; ++n1) rowp[4 * n1].x = x[n1].x;
+            // real phase out through shared memory: every thread has read its
+            // row cells, the real parts go to compact rows (stride S values,
+            // bank-conflict free for the row roles) in the space of Z, and
+            // pairs of values leave with coalesced 8- or 16-byte stores
             __syncthreads();
-            T* ph = phase;
-            for (int c = tid; c < N * N / 4; c += NT) {
-                const V* zr = Z + ((4 * c) / N) * S + (4 * c) % N;
-                store4(ph + 4 * c, zr[0].x, zr[1].x, zr[2].x, zr[3].x);
+            T* const Zf = reinterpret_cast<T*>(Z);
+            T* const rowf = Zf + r * S + n2;
+#pragma unroll
+            for (int n1 = 0; n1 < R; ++n1) rowf[4 * n1] = x[n1].x;
+            __syncthreads();
+            V* const ph2 = reinterpret_cast<V*>(phase);
+            for (int c = tid; c < N * N / 2; c += NT) {
+                const int row = (2 * c) / N, col = (2 * c) % N;
+                ph2[c] = *reinterpret_cast<const V*>(Zf + row * S + col);
             }
         }
     }

@@ -33,6 +33,7 @@ template <typename T> struct Params {
     T* ext_out = nullptr;                // [F][2][N][N] or nullptr
     int n = 0, off = 0, F = 0, iters = 0, periodic = 0;
     unsigned* status = nullptr;          // sticky device status bits
+    int wf_smem = 0;                     // fused kernel: final weights resident in shared memory (set by its launcher)
 };
 
 // Where Eq. PC is applied (same values as FWR_PERIODIC_* in fwr.h).

@@ -30,8 +30,10 @@
 
 namespace {
 
-using fwr::umma::BK;
 using fwr::umma::BM;
+
+// K elements per pipeline stage of the tensor-core GEMM (32: 64-byte swizzle)
+constexpr int GEMM_BK = 64;
 
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -53,23 +55,23 @@ EncodeTiledFn encode_fn() {
 }
 
 // BF16 matrix [rows][ld] (ld elements per row, ld * 2 a multiple of 16) read
-// as {cols, rows} in boxes of 64 x box_rows with the 128-byte swizzle
+// as {cols, rows} in boxes of GEMM_BK x box_rows with the matching swizzle
 bool make_map(CUtensorMap* map, const void* ptr, uint64_t cols, uint64_t rows, uint64_t ld, int box_rows) {
     EncodeTiledFn enc = encode_fn();
     if (!enc) return false;
     const cuuint64_t dims[2] = {cols, rows};
     const cuuint64_t strides[1] = {ld * 2};
-    const cuuint32_t box[2] = {uint32_t(BK), uint32_t(box_rows)};
+    const cuuint32_t box[2] = {uint32_t(GEMM_BK), uint32_t(box_rows)};
     const cuuint32_t estr[2] = {1, 1};
     return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, estr,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+               CU_TENSOR_MAP_INTERLEAVE_NONE, GEMM_BK == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 template <int BN, typename OutT>
 cudaError_t set_smem() {
-    return cudaFuncSetAttribute(fwr::umma::gemm_kernel<BN, OutT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                int(fwr::umma::Cfg<BN>::SMEM));
+    return cudaFuncSetAttribute(fwr::umma::gemm_kernel<BN, GEMM_BK, OutT>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, int(fwr::umma::Cfg<BN, GEMM_BK>::SMEM));
 }
 
 // per device: the kernels' shared-memory limit is raised once; SM count
@@ -102,29 +104,30 @@ cudaError_t launch_gemm(const CUtensorMap& ma, const CUtensorMap& mb128, const C
     const long long tiles = tm * (N / bn);
     const unsigned grid = unsigned(tiles < sms ? tiles : sms);
     if (bn == 256)
-        fwr::umma::gemm_kernel<256, OutT><<<grid, fwr::umma::THREADS, fwr::umma::Cfg<256>::SMEM, s>>>(
-            ma, mb256, M, int(N), K, D, ldd, status);
+        fwr::umma::gemm_kernel<256, GEMM_BK, OutT>
+            <<<grid, fwr::umma::THREADS, fwr::umma::Cfg<256, GEMM_BK>::SMEM, s>>>(ma, mb256, M, int(N), K, D, ldd,
+                                                                              status);
     else
-        fwr::umma::gemm_kernel<128, OutT><<<grid, fwr::umma::THREADS, fwr::umma::Cfg<128>::SMEM, s>>>(
-            ma, mb128, M, int(N), K, D, ldd, status);
+        fwr::umma::gemm_kernel<128, GEMM_BK, OutT>
+            <<<grid, fwr::umma::THREADS, fwr::umma::Cfg<128, GEMM_BK>::SMEM, s>>>(ma, mb128, M, int(N), K, D, ldd,
+                                                                              status);
     return cudaGetLastError();
 }
 
-// slopes [F][2][n][n] -> X [F][ldx] BF16: column j < nv the x slope of valid
-// cell cells[j], nv <= j < 2 nv the y slope of cells[j - nv], zero beyond.
+// slopes [F][2][n][n] -> X [F][ldx] BF16: column j takes the slope at
+// offset src[j] of the frame's [2][n][n] block (x slopes of the valid cells in
+// row-major order, then their y slopes), or 0 where src[j] < 0 (padding).
 // One block per frame; pairs of columns per thread (ldx even).
-__global__ void k_gather(const float* sl, const int* cells, int nv, int nn, int ldx, __nv_bfloat16* X) {
+__global__ void k_gather(const float* __restrict__ sl, const int2* __restrict__ src, int nn, int ldx,
+                         __nv_bfloat16* __restrict__ X) {
     const int f = blockIdx.x;
     const float* s = sl + size_t(f) * 2 * nn;
     __nv_bfloat162* x = reinterpret_cast<__nv_bfloat162*>(X + size_t(f) * ldx);
-    for (int j = 2 * threadIdx.x; j < ldx; j += 2 * blockDim.x) {
-        float v[2];
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-            const int jj = j + u;
-            v[u] = jj < nv ? s[cells[jj]] : jj < 2 * nv ? s[nn + cells[jj - nv]] : 0.f;
-        }
-        x[j >> 1] = __floats2bfloat162_rn(v[0], v[1]);
+#pragma unroll 4
+    for (int j = threadIdx.x; j < ldx / 2; j += blockDim.x) {
+        const int2 o = __ldg(src + j);
+        const float a = o.x >= 0 ? __ldg(s + o.x) : 0.f, b = o.y >= 0 ? __ldg(s + o.y) : 0.f;
+        x[j] = __floats2bfloat162_rn(a, b);
     }
 }
 
@@ -153,7 +156,7 @@ fwr_status fail(fwr_status code, const char* msg) {
 struct fwr_linws {
     int n = 0, N = 0, nv = 0, K = 0, Kpad = 0, rank = 0, max_batch = 0, device = 0;
     long long cells2 = 0;                 // 2 N^2
-    int* d_cells = nullptr;               // valid lenslet cells, row-major
+    int* d_src = nullptr;                 // [Kpad] source offset of every X column in a frame's slopes, or -1
     __nv_bfloat16* X = nullptr;           // [max_batch][Kpad]
     __nv_bfloat16* C = nullptr;           // [max_batch][rank]
     __nv_bfloat16* At = nullptr;          // [rank][Kpad]
@@ -167,7 +170,7 @@ struct fwr_linws {
 namespace {
 
 void free_ws(fwr_linws* w) {
-    cudaFree(w->d_cells);
+    cudaFree(w->d_src);
     cudaFree(w->X);
     cudaFree(w->C);
     cudaFree(w->At);
@@ -253,18 +256,23 @@ fwr_status fwr_linws_create(fwr_linws** out, const fwr_plan* plan, int rank, con
         if (w->mask[i]) cells.push_back(i);
     w->nv = int(cells.size());
     w->K = 2 * w->nv;
-    w->Kpad = (w->K + BK - 1) / BK * BK;
+    w->Kpad = (w->K + 63) / 64 * 64;
     auto alloc = [&](void** p, size_t bytes) {
         if (e == cudaSuccess) e = cudaMalloc(p, bytes);
     };
-    alloc(reinterpret_cast<void**>(&w->d_cells), cells.size() * sizeof(int));
+    alloc(reinterpret_cast<void**>(&w->d_src), size_t(w->Kpad) * sizeof(int));
     alloc(reinterpret_cast<void**>(&w->X), size_t(max_batch) * w->Kpad * 2);
     alloc(reinterpret_cast<void**>(&w->C), size_t(max_batch) * rank * 2);
     alloc(reinterpret_cast<void**>(&w->At), size_t(rank) * w->Kpad * 2);
     alloc(reinterpret_cast<void**>(&w->V), size_t(w->cells2) * rank * 2);
     alloc(reinterpret_cast<void**>(&w->Eh), size_t(max_batch) * w->cells2 * 2);
     alloc(reinterpret_cast<void**>(&w->d_status), sizeof(int));
-    if (e == cudaSuccess) e = cudaMemcpy(w->d_cells, cells.data(), cells.size() * sizeof(int), cudaMemcpyHostToDevice);
+    std::vector<int> src(size_t(w->Kpad), -1);
+    for (int j = 0; j < w->nv; ++j) {
+        src[j] = cells[j];
+        src[w->nv + j] = w->n * w->n + cells[j];
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(w->d_src, src.data(), src.size() * sizeof(int), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(w->At, 0, size_t(rank) * w->Kpad * 2);
     if (e == cudaSuccess) e = cudaMemset(w->d_status, 0, sizeof(int));
     // A [K][rank] -> At [rank][Kpad]; V [2 N^2][rank] as is
@@ -300,7 +308,7 @@ namespace {
 // gather, X A, (X A) V^T -> out [F][2 N^2] (FP32 or BF16)
 template <typename OutT>
 cudaError_t run_ws(fwr_linws* w, const float* slopes, int F, OutT* out, cudaStream_t s) {
-    k_gather<<<F, 256, 0, s>>>(slopes, w->d_cells, w->nv, w->n * w->n, w->Kpad, w->X);
+    k_gather<<<F, 256, 0, s>>>(slopes, reinterpret_cast<const int2*>(w->d_src), w->n * w->n, w->Kpad, w->X);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess)
         e = launch_gemm<__nv_bfloat16>(w->mX, w->mAt128, w->mAt256, F, w->rank, w->Kpad, w->C, w->rank, w->d_status,
@@ -330,7 +338,8 @@ fwr_status fwr_linws_reconstruct(fwr_linws* w, fwr_plan* plan, const float* slop
     if (plan->n != w->n || plan->N != w->N || plan->h_mask != w->mask)
         return fail(FWR_ERR_ARG, "fwr_linws_reconstruct: the plan's pupil or grid differs from the warm start's");
     if (n_frames == 0) return FWR_OK;
-    if (!slopes_dev || !phase_dev) return fail(FWR_ERR_ARG, "fwr_linws_reconstruct: null pointer");
+    if (!slopes_dev || !phase_dev || !aligned16(phase_dev))
+        return fail(FWR_ERR_ARG, "fwr_linws_reconstruct: null or unaligned pointer");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e = run_ws<__nv_bfloat16>(w, slopes_dev, n_frames, w->Eh, s);
     if (e == cudaSuccess)

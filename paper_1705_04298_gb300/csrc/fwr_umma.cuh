@@ -5,9 +5,9 @@
 // Persistent and warp-specialised: one CTA per SM walks the 128 x BN output
 // tiles t = blockIdx.x, blockIdx.x + gridDim.x, ... (M-tile fastest, so CTAs
 // running at the same time share the B tile in L2). Six warps:
-//   warp 0, lane 0   producer: TMA loads of the A (64 x 128) and B (64 x BN)
-//                    k-blocks (64 K elements = one 128-byte swizzle row) into
-//                    a ring of STAGES shared-memory stages, across tile
+//   warp 0, lane 0   producer: TMA loads of the A (BK x 128) and B (BK x BN)
+//                    k-blocks (BK = 64 or 32 K elements: one 128- or 64-byte
+//                    swizzle row) into a ring of shared-memory stages, across tile
 //                    boundaries; completion counted on the stage's "full"
 //                    mbarrier
 //   warp 1, lane 0   issuer: four tcgen05.mma (M 128, N BN, K 16) per k-block
@@ -16,20 +16,23 @@
 //                    a tile's last k-block, to the accumulator's "full" barrier
 //   warps 2-5        epilogue: tcgen05.ld of their 32 accumulator lanes
 //                    (rows; warp w reads lanes 32 (w mod 4) ..), conversion,
-//                    row-wise stores, then an arrive on the accumulator's
-//                    "empty" barrier, so the next tile's MMAs run meanwhile
+//                    a pass through a swizzled shared tile so that each store
+//                    instruction writes four whole 128-byte rows, then an
+//                    arrive on the accumulator's "empty" barrier, so the next
+//                    tile's MMAs run meanwhile
 // Every mbarrier wait gives up after about two seconds (clock64), sets the
 // CTA's abort flag and the caller's status word; the roles then skip their
 // work, the producer waits (bounded) for its loads in flight, the issuer for
 // its MMAs, and the TMEM is freed before the CTA returns.
 //
-// Shared-memory operand layout: the canonical K-major 128-byte-swizzle layout
-// that TMA writes with CU_TENSOR_MAP_SWIZZLE_128B for a box of 64 x rows: row
-// r at byte 128 r, its 16-byte chunk c at chunk position c ^ (r mod 8), stage
-// bases 1024-byte aligned. The matrix descriptor carries the start address,
-// an 8-row stride of 1024 bytes and the swizzle mode; the k-th 16-element
-// slice of the 64-element row is the start address plus 32 k bytes (the
-// swizzle is applied to the final address).
+// Shared-memory operand layout: the canonical K-major swizzled layout that TMA
+// writes with CU_TENSOR_MAP_SWIZZLE_128B (64 x rows boxes, rows of 128 bytes,
+// 16-byte chunk c of row r at chunk position c ^ (r mod 8)) or _64B (32 x rows
+// boxes, rows of 64 bytes, chunk c at c ^ ((r / 2) mod 4)); stage bases are
+// 1024-byte aligned. The matrix descriptor carries the start address, the
+// 8-row stride (1024 or 512 bytes) and the swizzle mode; the k-th 16-element
+// slice of a row is the start address plus 32 k bytes (the swizzle is applied
+// to the final address).
 #pragma once
 
 #include <cuda.h>
@@ -40,22 +43,32 @@
 namespace fwr {
 namespace umma {
 
-constexpr int BM = 128, BK = 64, THREADS = 192;
+constexpr int BM = 128, THREADS = 192;
 constexpr long long WAIT_LIMIT = 4000000000LL;  // cycles (about 2 s at 2 GHz)
 
-// Per-BN configuration (BN = 128 or 256): 192 KB of stages either way
-template <int BN>
+// Per-(BN, BK) configuration: BN = 128 or 256 output columns per tile, BK =
+// 64 K elements per stage (128-byte rows, 128-byte swizzle) or 32 (64-byte
+// rows, 64-byte swizzle: half the bytes per stage, twice the stages in the
+// same 192 KB, so more TMA latency is covered).
+template <int BN, int BK>
 struct Cfg {
     static_assert(BN == 128 || BN == 256, "tile width");
+    static_assert(BK == 32 || BK == 64, "k-block");
     static constexpr uint32_t A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2, STAGE_BYTES = A_BYTES + B_BYTES;
-    static constexpr int STAGES = BN == 256 ? 4 : 6;
+    static constexpr int STAGES = int(196608u / STAGE_BYTES);
     static constexpr uint32_t TMEM_COLS = 2 * BN;
     // kind::f16 instruction descriptor: FP32 accumulator, BF16 A and B, both
     // K-major, N = BN, M = BM
     static constexpr uint32_t IDESC =
         (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(BN >> 3) << 17) | (uint32_t(BM >> 4) << 24);
-    // stages + 1 KB alignment slack + barriers and flags
-    static constexpr size_t SMEM = size_t(STAGES) * STAGE_BYTES + 1024 + 256;
+    // matrix descriptor: 8-row groups 8 x (2 BK) bytes apart; swizzle mode
+    // 2 = 128-byte, 4 = 64-byte
+    static constexpr uint32_t SBO = 8 * 2 * BK;
+    static constexpr uint64_t SWIZZLE = BK == 64 ? 2 : 4;
+    // epilogue staging: 32 rows x 128 bytes per epilogue warp
+    static constexpr uint32_t EPI_BYTES = 4 * 32 * 128;
+    // stages + epilogue staging + 1 KB alignment slack + barriers and flags
+    static constexpr size_t SMEM = size_t(STAGES) * STAGE_BYTES + EPI_BYTES + 1024 + 512;
 };
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return uint32_t(__cvta_generic_to_shared(p)); }
@@ -99,13 +112,14 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
         : "memory");
 }
 
-// K-major, 128-byte swizzle, 8-row groups 1024 bytes apart
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+// K-major shared-memory matrix descriptor: start address, 8-row stride sbo,
+// swizzle mode
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t sbo, uint64_t swizzle) {
     uint64_t d = uint64_t((saddr & 0x3FFFFu) >> 4);
     d |= uint64_t(1) << 16;            // leading-dimension offset (16 B; not used by swizzled K-major)
-    d |= uint64_t(1024 >> 4) << 32;    // stride-dimension offset
+    d |= uint64_t(sbo >> 4) << 32;     // stride-dimension offset
     d |= uint64_t(1) << 46;            // descriptor version
-    d |= uint64_t(2) << 61;            // 128-byte swizzle
+    d |= swizzle << 61;
     return d;
 }
 
@@ -141,21 +155,18 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
 
+// Output values per 128-byte row segment: 32 FP32 or 64 BF16
 template <typename OutT>
-__device__ __forceinline__ void store32(OutT* dst, const uint32_t (&v)[32]);
+struct Epi {
+    static constexpr int COLS = 128 / int(sizeof(OutT));
+};
 
-template <>
-__device__ __forceinline__ void store32<float>(float* dst, const uint32_t (&v)[32]) {
-    float4* d = reinterpret_cast<float4*>(dst);
+// Pack 32 FP32 accumulator values as 8 16-byte chunks (FP32) or 4 (BF16).
+__device__ __forceinline__ void pack_chunks(const uint32_t (&v)[32], uint4* out, float*) {
 #pragma unroll
-    for (int i = 0; i < 8; ++i)
-        d[i] = make_float4(__uint_as_float(v[4 * i]), __uint_as_float(v[4 * i + 1]), __uint_as_float(v[4 * i + 2]),
-                           __uint_as_float(v[4 * i + 3]));
+    for (int i = 0; i < 8; ++i) out[i] = make_uint4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
 }
-
-template <>
-__device__ __forceinline__ void store32<__nv_bfloat16>(__nv_bfloat16* dst, const uint32_t (&v)[32]) {
-    uint4* d = reinterpret_cast<uint4*>(dst);
+__device__ __forceinline__ void pack_chunks(const uint32_t (&v)[32], uint4* out, __nv_bfloat16*) {
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         uint32_t w[4];
@@ -165,8 +176,44 @@ __device__ __forceinline__ void store32<__nv_bfloat16>(__nv_bfloat16* dst, const
                 __floats2bfloat162_rn(__uint_as_float(v[8 * i + 2 * j]), __uint_as_float(v[8 * i + 2 * j + 1]));
             w[j] = *reinterpret_cast<const uint32_t*>(&h);
         }
-        d[i] = make_uint4(w[0], w[1], w[2], w[3]);
+        out[i] = make_uint4(w[0], w[1], w[2], w[3]);
     }
+}
+
+// One 128-byte-wide column segment of a warp's 32 accumulator rows to global
+// memory: TMEM -> registers (the lane's row) -> shared tile (16-byte chunk c
+// of row r at chunk position c ^ (r mod 8): conflict free both ways) -> rows
+// written whole, 8 lanes per 128-byte row, 4 rows per store instruction.
+// tw: TMEM address of the warp's lanes at the segment's first column; dst:
+// the segment's first column in row m0w (the warp's first row); rows at or
+// beyond M are not stored.
+template <typename OutT>
+__device__ __forceinline__ void epilogue_segment(uint32_t tw, uint4* tile, OutT* dst, long long ldd, int m0w, int M,
+                                                 int lane) {
+    uint4 ch[8];
+    {
+        uint32_t v[32];
+        tmem_ld32(tw, v);
+        pack_chunks(v, ch, static_cast<OutT*>(nullptr));
+    }
+    if (sizeof(OutT) == 2) {
+        uint32_t v[32];
+        tmem_ld32(tw + 32u, v);
+        pack_chunks(v, ch + 4, static_cast<OutT*>(nullptr));
+    }
+#pragma unroll
+    for (int c = 0; c < 8; ++c) tile[lane * 8 + (c ^ (lane & 7))] = ch[c];
+    __syncwarp();
+    const int c = lane & 7;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int r = 4 * i + (lane >> 3);
+        if (m0w + r < M) {
+            const uint4 val = tile[r * 8 + (c ^ (r & 7))];
+            *reinterpret_cast<uint4*>(reinterpret_cast<uint8_t*>(dst + (m0w + r) * ldd) + 16 * c) = val;
+        }
+    }
+    __syncwarp();
 }
 
 // bounded wait without an abort check (draining work already issued)
@@ -182,11 +229,11 @@ __device__ __forceinline__ void mbar_drain(uint32_t bar, uint32_t parity, volati
 // D[M][ldd] = A B^T over K, N a multiple of BN. The maps describe A as {K, M}
 // with box {64, 128} and B as {K, N} with box {64, BN}; K beyond the tensors'
 // extent and rows beyond M read as zeros (TMA fill) and are not stored.
-template <int BN, typename OutT>
+template <int BN, int BK, typename OutT>
 __global__ void __launch_bounds__(THREADS, 1)
     gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int M, int N,
                 int K, OutT* __restrict__ D, long long ldd, int* status) {
-    typedef Cfg<BN> C;
+    typedef Cfg<BN, BK> C;
     constexpr int S = C::STAGES;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = su32(smem_raw);
@@ -194,7 +241,8 @@ __global__ void __launch_bounds__(THREADS, 1)
     uint8_t* const gbase = smem_raw + (base - raw);
     // barriers: full[S], empty[S], acc_full[2], acc_empty[2], mma_done; then
     // the TMEM address and the abort flag
-    uint64_t* const bars = reinterpret_cast<uint64_t*>(gbase + S * C::STAGE_BYTES);
+    uint4* const epi = reinterpret_cast<uint4*>(gbase + S * C::STAGE_BYTES);
+    uint64_t* const bars = reinterpret_cast<uint64_t*>(gbase + S * C::STAGE_BYTES + C::EPI_BYTES);
     uint32_t* const tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * S + 5);
     volatile int* const abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
     const uint32_t full0 = su32(bars), empty0 = full0 + 8 * S, accf0 = empty0 + 8 * S, acce0 = accf0 + 16,
@@ -271,7 +319,8 @@ __global__ void __launch_bounds__(THREADS, 1)
                     const uint32_t sa = base + s * C::STAGE_BYTES, sb = sa + C::A_BYTES;
 #pragma unroll
                     for (int k = 0; k < BK / 16; ++k)
-                        mma_bf16(d, sdesc(sa + 32u * k), sdesc(sb + 32u * k), C::IDESC, (kb > 0 || k > 0) ? 1u : 0u);
+                        mma_bf16(d, sdesc(sa + 32u * k, C::SBO, C::SWIZZLE), sdesc(sb + 32u * k, C::SBO, C::SWIZZLE),
+                                 C::IDESC, (kb > 0 || k > 0) ? 1u : 0u);
                     mma_commit(empty0 + 8 * s);
                 }
                 if (ok) mma_commit(accf0 + 8 * b);
@@ -291,14 +340,11 @@ __global__ void __launch_bounds__(THREADS, 1)
             if (!ok) break;
             fence_after();
             const int m0 = (t % tiles_m) * BM, n0 = (t / tiles_m) * BN;
-            const int row = m0 + q * 32 + lane;
             const uint32_t tw = tmem + uint32_t(b * BN) + (uint32_t(q * 32) << 16);
+            uint4* const tile = epi + (warp - 2) * 256;
 #pragma unroll 1
-            for (int c = 0; c < BN; c += 32) {
-                uint32_t v[32];
-                tmem_ld32(tw + uint32_t(c), v);
-                if (row < M) store32<OutT>(D + row * ldd + n0 + c, v);
-            }
+            for (int c = 0; c < BN; c += Epi<OutT>::COLS)
+                epilogue_segment<OutT>(tw + uint32_t(c), tile, D + n0 + c, ldd, m0 + q * 32, M, lane);
             fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(acce0 + 8 * b);

@@ -17,8 +17,8 @@ the truncation keeps what turbulence-like slopes excite. The fit is off-line
 host work in FP64 (numpy); inference runs entirely in the library
 (fwr_linws_forward, then fwr_reconstruct_ex).
 
-    python -m paper_1705_04298_gb300.linws eval --rank 1280
-    python -m paper_1705_04298_gb300.linws time --rank 1280 --reps 20
+    python -m paper_1705_04298_gb300.linws eval --rank 1152
+    python -m paper_1705_04298_gb300.linws time --rank 1152 --reps 20
 """
 
 import argparse
@@ -30,9 +30,9 @@ import numpy as np
 
 from . import learned
 
-TRAIN_FRAMES = 4096
+TRAIN_FRAMES = 8192
 OPERATOR_ITERS = 10
-DEFAULT_RANK = 1280
+DEFAULT_RANK = 1152
 
 
 def valid_cells(mask):
@@ -94,7 +94,8 @@ def fit(E, X, rank):
 def build(fwr, plan, mask, rank=DEFAULT_RANK, max_batch=1000, frames=TRAIN_FRAMES, iters=OPERATOR_ITERS,
           log=None):
     """Operator from the library, training slopes from the seeded generator
-    (seeds 1e6 + i, noise cycling 0.02, 0.05, 0.1 rad), fit, device object."""
+    (seeds 1e6 + i, noise cycling 0.02, 0.05, 0.1 rad; 8192 frames by default),
+    fit, device object."""
     from . import synth
     t0 = time.time()
     E = extension_operator(fwr, plan, mask, iters)

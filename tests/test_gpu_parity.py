@@ -284,3 +284,21 @@ def test_256_grid_persistent_tail_and_limits(fwr):
     with pytest.raises(fwr.FwrError):
         plan.reconstruct(torch.zeros((1, 2, n, n), device="cuda"), 1,
                          ext_out=torch.empty((1, 2, 256, 256), device="cuda"))
+
+
+def test_misaligned_phase_and_warm_start_are_refused(fwr):
+    """The kernels store the phase and read the warm start with 16-byte
+    vector accesses; pointers off that alignment are argument errors."""
+    n = 16
+    fr = synth.frame(n, 3, 0.05)
+    plan = fwr.Plan(fr["mask"], 2.0, fwr.LSQ)
+    N = plan.N
+    s = torch.tensor(fr["slopes"][None], dtype=torch.float32, device="cuda")
+    flat = torch.empty(N * N + 1, dtype=torch.float32, device="cuda")
+    with pytest.raises(fwr.FwrError):
+        plan.reconstruct(s, 2, flat[1:].view(1, N, N))
+    ext = torch.zeros(2 * N * N + 1, dtype=torch.float32, device="cuda")
+    with pytest.raises(fwr.FwrError):
+        plan.reconstruct(s, 2, ext_init=ext[1:].view(1, 2, N, N))
+    ok = plan.reconstruct(s, 2, flat[:N * N].view(1, N, N))
+    assert torch.isfinite(ok).all()
