@@ -202,7 +202,8 @@ def extra_measurements(fwr, synth, torch, flush):
     flushed): 40x40 at each iteration count, the 16x16 single-frame latency
     (FP32 and FP64), a ragged 4096-frame batch of 40/64/80/128-lenslet pupils
     (one graph-captured launch, autotuned schedule) and 128x128 lenslets on a
-    256^2 grid with 10 iterations. The warm starts are measured by
+    256^2 grid with 10 iterations, with the FFT and with the split-BF16
+    DFT-as-GEMM transform. The warm starts are measured by
     learned_measurements."""
     peak = fp32_peak_tflops()
     res = {}
@@ -279,6 +280,19 @@ def extra_measurements(fwr, synth, torch, flush):
     tf = flops_per_frame(256, 10) * 1000 / (ms / 1e3) / 1e12
     res["128x128_256grid_k10_frozen_flow"] = {"frames_per_s": 1000 / (ms / 1e3), "ms": ms, "tflops": tf,
                                               "frac": tf / peak}
+    # the same frames through the split-BF16 DFT-as-GEMM transform (batched
+    # tcgen05 GEMMs): 2 GEMMs per 2-D transform, 2 (k + 1) transforms, each
+    # GEMM 2 x (2N) x (6N) x N flop per frame
+    p4.set_transform(fwr.TRANSFORM_DFT_BF16X3)
+    p4.reconstruct(s4, 10, ph4)
+    ms = _time_launches(lambda: p4.reconstruct(s4, 10, ph4), flush, 3, torch)
+    bpeak, bsrc = measured_bf16_peak()
+    gfl = 2 * (10 + 1) * 2 * (2.0 * 512 * 1536 * 256) * 1000
+    res["128x128_256grid_k10_frozen_flow_dft_bf16x3"] = {
+        "frames_per_s": 1000 / (ms / 1e3), "ms": ms,
+        "roofline": {"bound": "tensor", "achieved": gfl / (ms / 1e3) / 1e12, "peak": bpeak, "peak_source": bsrc,
+                     "unit": "TFLOP/s", "frac": gfl / (ms / 1e3) / 1e12 / bpeak, "flops_per_launch": gfl,
+                     "note": "GEMM flops only; element-wise kernels between the GEMMs are not counted"}}
     return res
 
 

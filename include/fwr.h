@@ -83,8 +83,14 @@ typedef enum {
 #define FWR_TRANSFORM_FFT 0         /* shared-memory FFT (default) */
 #define FWR_TRANSFORM_DFT_BF16X3 1  /* dense DFT products on the tensor cores with split-BF16
                                        operands (x = hi + lo, products hi*hi + hi*lo + lo*hi,
-                                       FP32 accumulation); N = 32 or 64 only
-                                       (FWR_ERR_UNSUPPORTED otherwise); about 1e-4 relative error */
+                                       FP32 accumulation). N = 32 or 64: per-frame mma.sync
+                                       products in one kernel. N = 128 or 256: batched tcgen05
+                                       GEMMs over chunks of frames (two per 2-D transform) with
+                                       element-wise kernels between them; setting the option
+                                       allocates the plan's workspace (about 170 MB) and the
+                                       reconstruct calls allocate nothing; no ext_out (returns
+                                       FWR_ERR_UNSUPPORTED). Other N: FWR_ERR_UNSUPPORTED.
+                                       About 1e-5 relative phase error (stated by the tests) */
 /* Values of FWR_OPT_PERIODIC: where Eq. PC is applied. */
 #define FWR_PERIODIC_BEFORE_EACH_FFT 0 /* before every forward FFT, the final one included (default) */
 #define FWR_PERIODIC_FINAL_ONLY 1      /* once, before the final reconstruction (Algorithm 1 step 5) */

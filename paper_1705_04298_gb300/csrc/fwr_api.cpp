@@ -254,6 +254,7 @@ void fwr_plan_destroy(fwr_plan* p) {
     cudaFree(p->d_mask);
     cudaFree(p->d_status);
     cudaFree(p->d_scratch);
+    cudaFree(p->d_dftws);
     cudaFree(p->d_stage_in);
     cudaFree(p->d_stage_out);
     cudaSetDevice(prev);
@@ -269,7 +270,22 @@ fwr_status fwr_plan_set_option(fwr_plan* p, int key, double value) {
     if (key == FWR_OPT_TRANSFORM) {
         const int v = int(value);
         if (double(v) != value || (v != FWR_TRANSFORM_FFT && v != FWR_TRANSFORM_DFT_BF16X3)) return FWR_ERR_ARG;
-        if (v == FWR_TRANSFORM_DFT_BF16X3 && p->N != 32 && p->N != 64) return FWR_ERR_UNSUPPORTED;
+        if (v == FWR_TRANSFORM_DFT_BF16X3 && p->N != 32 && p->N != 64 && p->N != 128 && p->N != 256)
+            return FWR_ERR_UNSUPPORTED;
+        if (v == FWR_TRANSFORM_DFT_BF16X3 && p->N >= 128 && !p->d_dftws) {
+            // batched tensor-core path: its workspace is made here, not in the reconstruct calls
+            int prev = 0;
+            cudaGetDevice(&prev);
+            cudaSetDevice(p->device);
+            cudaError_t e = cudaMalloc(&p->d_dftws, fwr::dftgemm_ws_bytes(p->N));
+            if (e == cudaSuccess) e = fwr::dftgemm_setup(p->N, p->f32.tw, p->d_dftws);
+            if (e != cudaSuccess) {
+                cudaFree(p->d_dftws);
+                p->d_dftws = nullptr;
+            }
+            cudaSetDevice(prev);
+            if (e != cudaSuccess) return cuda_fail(e, "DFT-GEMM workspace");
+        }
         p->transform = v;
         return FWR_OK;
     }
@@ -316,7 +332,12 @@ fwr_status fwr_reconstruct_ex(fwr_plan* p, const float* slopes, const float* ext
     k.status = p->d_status;
     cudaError_t e;
     if (p->transform == FWR_TRANSFORM_DFT_BF16X3) {
-        e = fwr::launch_basic_gemm_f32(p->N, k, static_cast<cudaStream_t>(stream));
+        if (p->N >= 128) {
+            if (ext_out || !phase) return FWR_ERR_UNSUPPORTED;
+            e = fwr::launch_dftgemm_f32(p->N, k, p->d_dftws, static_cast<cudaStream_t>(stream));
+        } else {
+            e = fwr::launch_basic_gemm_f32(p->N, k, static_cast<cudaStream_t>(stream));
+        }
     } else if (p->N == 256) {
         if (ext_out || !phase) return FWR_ERR_UNSUPPORTED;
         e = fwr::launch_slab(k, p->d_scratch, p->scratch_ctas, static_cast<cudaStream_t>(stream));

@@ -1,0 +1,287 @@
+// Split-BF16 DFT-as-GEMM path for 128^2 and 256^2 grids on the tcgen05 tensor
+// cores: Algorithm 1 (Sec. 3.3) and the final reconstruction (Eqs. 2-3) with
+// every 2-D DFT computed as dense products, Z <- F Z F with F[j][k] =
+// e^{-2 i pi j k / N} (the conjugate for the inverse; no scaling: 1/N^2 is in
+// the spectral weights).
+//
+// The frames of a chunk are the columns of two GEMMs per 2-D transform (D =
+// A B^T, fwr_umma.cuh). A complex N x N product is one real 2N x 2N product:
+// [Re; Im] <- [[Fr, -Fi], [Fi, Fr]] [Re; Im]. Every FP32 operand x is split as
+// hi + lo (hi = bf16(x), lo = bf16(x - hi)) and the three products hi hi +
+// hi lo + lo hi are one GEMM over K = 6N: A = [Ah | Ah | Al], B rows =
+// [hi | lo | hi] (the lo lo term, about 2^-16 relative, is dropped). FP32
+// accumulation in TMEM.
+//
+// Per transform, with the chunk's frames f and row (or column) index x:
+//   right product  B rows (f, r) = row r of Z_f        -> D [2N][(f, r)] = (Z_f F)^T
+//   left product   B rows (f, i) = column i of Z_f F   -> D [2N][(f, k)] = F Z_f F
+// so D's rows are output rows (real parts, then imaginary parts) and its
+// columns run over frames and the other index. Between the GEMMs, element-wise
+// kernels rebuild B from D: the plain re-split, the spectral step (LSQ
+// projection or final filter, with the y part of Eq. PC as a spectral
+// correction) and, in direct space, reinsertion of the measured slopes and the
+// x part of Eq. PC.
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fwr_internal.h"
+
+namespace fwr {
+
+#include "fwr_fft.cuh"
+
+namespace {
+
+typedef __nv_bfloat16 bf16;
+
+// frames per chunk: the chunk's GEMMs have 2^23 / N columns
+__host__ __device__ inline int chunk_frames(int N) { return (1 << 23) / (N * N); }
+
+struct Ws {
+    bf16* Af;  // [2N][6N] forward operand
+    bf16* Ai;  // [2N][6N] inverse operand
+    bf16* B;   // [chunk N][6N]
+    float* D;  // [2N][chunk N]
+};
+
+Ws carve(int N, void* ws) {
+    Ws w;
+    uint8_t* p = static_cast<uint8_t*>(ws);
+    const size_t a = size_t(2 * N) * 6 * N * sizeof(bf16);
+    const size_t cols = size_t(chunk_frames(N)) * N;
+    w.Af = reinterpret_cast<bf16*>(p);
+    w.Ai = reinterpret_cast<bf16*>(p + a);
+    w.B = reinterpret_cast<bf16*>(p + 2 * a);
+    w.D = reinterpret_cast<float*>(p + 2 * a + cols * 6 * N * sizeof(bf16));
+    return w;
+}
+
+__device__ __forceinline__ void split(float x, bf16& hi, bf16& lo) {
+    hi = __float2bfloat16_rn(x);
+    lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+}
+
+// entry k of a B row of length 6N: [hi | lo | hi]
+__device__ __forceinline__ void put_split(bf16* row, int N, int k, float x) {
+    bf16 h, l;
+    split(x, h, l);
+    row[k] = h;
+    row[2 * N + k] = l;
+    row[4 * N + k] = h;
+}
+
+// A operands from the twiddle table: forward [[Fr, -Fi], [Fi, Fr]], inverse
+// with Fi -> -Fi; rows [Ah | Ah | Al].
+__global__ void k_dg_operands(const float2* tw, int N, bf16* Af, bf16* Ai) {
+    const int i = blockIdx.x;  // output row 0 .. 2N
+    for (int c = threadIdx.x; c < 2 * N; c += blockDim.x) {
+        const int io = i % N, co = c % N;
+        const float2 f = tw[(long long)io * co % N];  // (cos, -sin) of 2 pi io co / N
+        const bool im_out = i >= N, im_in = c >= N;
+        // forward: Re out = Fr Re - Fi Im, Im out = Fi Re + Fr Im (Fi = f.y)
+        const float vf = im_out == im_in ? f.x : (im_out ? f.y : -f.y);
+        const float vi = im_out == im_in ? f.x : (im_out ? -f.y : f.y);
+        bf16 h, l;
+        split(vf, h, l);
+        Af[(size_t)i * 6 * N + c] = h;
+        Af[(size_t)i * 6 * N + 2 * N + c] = h;
+        Af[(size_t)i * 6 * N + 4 * N + c] = l;
+        split(vi, h, l);
+        Ai[(size_t)i * 6 * N + c] = h;
+        Ai[(size_t)i * 6 * N + 2 * N + c] = h;
+        Ai[(size_t)i * 6 * N + 4 * N + c] = l;
+    }
+}
+
+// Direct-space rows -> B rows (f, r) of the right product. Source: the embed
+// (first pass: measured slopes in the pupil, warm start or 0 outside) or D in
+// the direct-space layout of the previous inverse (then the measured slopes
+// are reinserted). Then the x part of Eq. PC when `fill`. One block of N / 2
+// threads per row.
+__global__ void k_dg_rows(const float* D, long long ldd, bool embed, const float* slopes, const float* ext,
+                          const uint8_t* mask, int n, int off, int N, int f0, bool fill, bf16* B,
+                          unsigned* status) {
+    const int row = blockIdx.x;  // (f, r) in the chunk
+    const int fl = row / N, r = row % N, f = f0 + fl;
+    const int nn = n * n;
+    const float* sl = slopes + (size_t)f * 2 * nn;
+    __shared__ float red[32];
+    float xs[2], ys[2];
+    float part = 0.f;
+    bool bad = false;
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        const int c = threadIdx.x + u * (N / 2);
+        float vx, vy;
+        if (embed) {
+            const float* e = ext ? ext + (size_t)f * 2 * N * N : nullptr;
+            vx = e ? e[r * N + c] : 0.f;
+            vy = e ? e[N * N + r * N + c] : 0.f;
+        } else {
+            vx = D[(size_t)r * ldd + (size_t)fl * N + c];
+            vy = D[(size_t)(N + r) * ldd + (size_t)fl * N + c];
+        }
+        const int i = r - off, j = c - off;
+        if (i >= 0 && i < n && j >= 0 && j < n && mask[i * n + j]) {
+            vx = sl[i * n + j];
+            vy = sl[nn + i * n + j];
+            bad |= !(isfinite(vx) && isfinite(vy));
+        }
+        xs[u] = vx;
+        ys[u] = vy;
+        if (c != N - 1) part += vx;
+    }
+    if (embed && bad) atomicOr(status, STATUS_NONFINITE);
+    if (fill) {
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+        __syncthreads();
+        if (threadIdx.x == N / 2 - 1) {
+            float s = 0.f;
+            for (int w = 0; w < N / 64; ++w) s += red[w];
+            xs[1] = -s;  // column N - 1 is this thread's second cell
+        }
+    }
+    bf16* b = B + (size_t)row * 6 * N;
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        const int c = threadIdx.x + u * (N / 2);
+        put_split(b, N, c, xs[u]);
+        put_split(b, N, N + c, ys[u]);
+    }
+}
+
+// D (rows: output index, real then imaginary; columns (f, x)) -> B rows
+// (f, i) = [Re D[i][(f, .)], Im D[N + i][(f, .)]] split: the next product's
+// operand. One block of N / 2 threads per B row.
+__global__ void k_dg_resplit(const float* D, long long ldd, int N, bf16* B) {
+    const int row = blockIdx.x;
+    const int fl = row / N, i = row % N;
+    bf16* b = B + (size_t)row * 6 * N;
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        const int x = threadIdx.x + u * (N / 2);
+        put_split(b, N, x, D[(size_t)i * ldd + (size_t)fl * N + x]);
+        put_split(b, N, N + x, D[(size_t)(N + i) * ldd + (size_t)fl * N + x]);
+    }
+}
+
+// Spectral step on Y_f[ky][kx] = D[ky][(f, kx)] + i D[N + ky][(f, kx)], the
+// packed spectrum of sx + i sy; writes B rows (f, ky) of the inverse's right
+// product. Non-final: LSQ projection (Algorithm 1 steps 2-3); final: the
+// filter of Eq. 2 (weights wfin). Both read the half-tables (rows ky <=
+// N / 2, the rest from (-ky, -kx)) that hold 1/N^2. With `fill`, the y part
+// of Eq. PC: Sy(ky, kx) -= Sy(0, kx) e^{2 i pi ky / N}.
+__global__ void k_dg_spectral(const float* D, long long ldd, int N, const Tables<float> tab, bool final, bool fill,
+                              bf16* B) {
+    const int row = blockIdx.x;  // (f, ky)
+    const int fl = row / N, ky = row % N, kyn = (N - ky) & (N - 1);
+    const float* wt = final ? tab.wfin : tab.iota;
+    bf16* b = B + (size_t)row * 6 * N;
+    const size_t cb = (size_t)fl * N;
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        const int kx = threadIdx.x + u * (N / 2), kxn = (N - kx) & (N - 1);
+        const float2 z1 = make_float2(D[(size_t)ky * ldd + cb + kx], D[(size_t)(N + ky) * ldd + cb + kx]);
+        const float2 z2 = make_float2(D[(size_t)kyn * ldd + cb + kxn], D[(size_t)(N + kyn) * ldd + cb + kxn]);
+        float2 sx = make_float2(0.5f * (z1.x + z2.x), 0.5f * (z1.y - z2.y));
+        float2 sy = make_float2(0.5f * (z1.y + z2.y), 0.5f * (z2.x - z1.x));
+        if (fill) {
+            const float2 e0 = make_float2(D[cb + kx], D[(size_t)N * ldd + cb + kx]);
+            const float2 e1 = make_float2(D[cb + kxn], D[(size_t)N * ldd + cb + kxn]);
+            const float2 ey = make_float2(0.5f * (e0.y + e1.y), 0.5f * (e1.x - e0.x));
+            const float2 t = tab.tw[ky];
+            const float2 c = cmul(ey, make_float2(t.x, -t.y));
+            sy = make_float2(sy.x - c.x, sy.y - c.y);
+        }
+        const float2 gx = cmul(tab.A[kx], tab.Tt[ky]);
+        const float2 gy = cmul(tab.Tt[kx], tab.A[ky]);
+        const float w = ky <= N / 2 ? wt[ky * N + kx] : wt[kyn * N + kxn];
+        float2 ph = cadd(cmulc(gx, sx), cmulc(gy, sy));
+        ph = make_float2(ph.x * w, ph.y * w);
+        float2 out;
+        if (!final) {
+            const float2 ox = cmul(gx, ph), oy = cmul(gy, ph);
+            out = make_float2(ox.x - oy.y, ox.y + oy.x);
+        } else {
+            out = ph;
+        }
+        put_split(b, N, kx, out.x);
+        put_split(b, N, N + kx, out.y);
+    }
+}
+
+// real phase of the chunk's frames out of the direct-space D
+__global__ void k_dg_phase(const float* D, long long ldd, int N, int f0, int nf, float* phase) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)nf * N * N) return;
+    const int fl = int(i / ((long long)N * N)), rc = int(i % ((long long)N * N)), r = rc / N, c = rc % N;
+    phase[(size_t)(f0 + fl) * N * N + rc] = D[(size_t)r * ldd + (size_t)fl * N + c];
+}
+
+}  // namespace
+
+size_t dftgemm_ws_bytes(int N) {
+    if (N != 128 && N != 256) return 0;
+    const size_t cols = size_t(chunk_frames(N)) * N;
+    return 2 * size_t(2 * N) * 6 * N * sizeof(bf16) + cols * 6 * N * sizeof(bf16) + size_t(2 * N) * cols * sizeof(float);
+}
+
+int dftgemm_chunk(int N) { return chunk_frames(N); }
+
+cudaError_t dftgemm_setup(int N, const float2* tw, void* ws) {
+    Ws w = carve(N, ws);
+    k_dg_operands<<<2 * N, 256>>>(tw, N, w.Af, w.Ai);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? cudaDeviceSynchronize() : e;
+}
+
+cudaError_t launch_dftgemm_f32(int N, const Params<float>& p, void* ws, cudaStream_t s) {
+    if ((N != 128 && N != 256) || !ws) return cudaErrorInvalidValue;
+    const Ws w = carve(N, ws);
+    const int chunk = chunk_frames(N);
+    const long long ldd = (long long)chunk * N;
+    int* st = reinterpret_cast<int*>(p.status);
+    for (int f0 = 0; f0 < p.F; f0 += chunk) {
+        const int nf = p.F - f0 < chunk ? p.F - f0 : chunk;
+        // GEMM columns: whole frames of N >= 128 columns, a multiple of 128
+        const long long cols = (long long)nf * N;
+        for (int it = 0; it <= p.iters; ++it) {
+            const bool final = it == p.iters;
+            const bool fill = p.periodic == PERIODIC_BEFORE_EACH_FFT || (p.periodic == PERIODIC_FINAL_ONLY && final);
+            k_dg_rows<<<nf * N, N / 2, 0, s>>>(w.D, ldd, it == 0, p.slopes, p.ext_init, p.mask, p.n, p.off, N, f0,
+                                               fill, w.B, p.status);
+            cudaError_t e = cudaGetLastError();
+            // forward transform: right product, re-split, left product
+            if (e == cudaSuccess) e = tc_gemm(w.Af, 2 * N, 6 * N, w.B, cols, w.D, false, ldd, st, s);
+            if (e == cudaSuccess) {
+                k_dg_resplit<<<nf * N, N / 2, 0, s>>>(w.D, ldd, N, w.B);
+                e = cudaGetLastError();
+            }
+            if (e == cudaSuccess) e = tc_gemm(w.Af, 2 * N, 6 * N, w.B, cols, w.D, false, ldd, st, s);
+            if (e == cudaSuccess) {
+                k_dg_spectral<<<nf * N, N / 2, 0, s>>>(w.D, ldd, N, p.tab, final, fill, w.B);
+                e = cudaGetLastError();
+            }
+            // inverse transform
+            if (e == cudaSuccess) e = tc_gemm(w.Ai, 2 * N, 6 * N, w.B, cols, w.D, false, ldd, st, s);
+            if (e == cudaSuccess) {
+                k_dg_resplit<<<nf * N, N / 2, 0, s>>>(w.D, ldd, N, w.B);
+                e = cudaGetLastError();
+            }
+            if (e == cudaSuccess) e = tc_gemm(w.Ai, 2 * N, 6 * N, w.B, cols, w.D, false, ldd, st, s);
+            if (e != cudaSuccess) return e;
+        }
+        if (p.phase) {
+            const long long tot = (long long)nf * N * N;
+            k_dg_phase<<<unsigned((tot + 255) / 256), 256, 0, s>>>(w.D, ldd, N, f0, nf, p.phase);
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+        }
+    }
+    return cudaSuccess;
+}
+
+}  // namespace fwr

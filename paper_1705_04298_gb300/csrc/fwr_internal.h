@@ -101,4 +101,19 @@ cudaError_t launch_fused_f64(int N, const Params<double>& p, cudaStream_t s);
 cudaError_t launch_fft2_f32(int N, const float2* in, float2* out, int F, int inverse,
                             const float2* tw, cudaStream_t s);
 
+// tcgen05 GEMM (fwr_linws.cu): D [M][ldd] = A [M][K] B [N][K]^T, A and B
+// BF16 row-major device arrays (16-byte aligned rows), K a multiple of 8, N
+// of 128; FP32 or BF16 output; a pipeline wait that runs out sets bit 2 of
+// *status.
+cudaError_t tc_gemm(const void* A, int M, int K, const void* B, long long N, void* D, bool bf16_out, long long ldd,
+                    int* status, cudaStream_t s);
+
+// Batched split-BF16 DFT-as-GEMM path for N = 128 and 256 (fwr_dftgemm_tc.cu):
+// every 2-D transform of Algorithm 1 and of the final reconstruction as two
+// tcgen05 GEMMs over a chunk of frames. Workspace: dftgemm_ws_bytes(N) bytes.
+size_t dftgemm_ws_bytes(int N);
+int dftgemm_chunk(int N);
+cudaError_t dftgemm_setup(int N, const float2* tw, void* ws);  // fills the DFT operand matrices of ws
+cudaError_t launch_dftgemm_f32(int N, const Params<float>& p, void* ws, cudaStream_t s);
+
 }  // namespace fwr

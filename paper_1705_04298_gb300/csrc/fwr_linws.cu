@@ -114,6 +114,25 @@ cudaError_t launch_gemm(const CUtensorMap& ma, const CUtensorMap& mb128, const C
     return cudaGetLastError();
 }
 
+}  // namespace
+
+// D [M][ldd] = A [M][K] B [N][K]^T (BF16 in, FP32 accumulate, FP32 or BF16
+// out), maps built per call; the library's other tensor-core users call this.
+cudaError_t fwr::tc_gemm(const void* A, int M, int K, const void* B, long long N, void* D, bool bf16_out,
+                         long long ldd, int* status, cudaStream_t s) {
+    if (M < 1 || K < 8 || K % 8 != 0 || N < 128 || N % 128 != 0) return cudaErrorInvalidValue;
+    CUtensorMap ma, mb128, mb256;
+    if (!make_map(&ma, A, uint64_t(K), uint64_t(M), uint64_t(K), BM) ||
+        !make_map(&mb128, B, uint64_t(K), uint64_t(N), uint64_t(K), 128) ||
+        !make_map(&mb256, B, uint64_t(K), uint64_t(N), uint64_t(K), 256))
+        return cudaErrorInvalidValue;
+    return bf16_out ? launch_gemm<__nv_bfloat16>(ma, mb128, mb256, M, N, K, static_cast<__nv_bfloat16*>(D), ldd,
+                                                 status, s)
+                    : launch_gemm<float>(ma, mb128, mb256, M, N, K, static_cast<float*>(D), ldd, status, s);
+}
+
+namespace {
+
 // slopes [F][2][n][n] -> X [F][ldx] BF16: column j takes the slope at
 // offset src[j] of the frame's [2][n][n] block (x slopes of the valid cells in
 // row-major order, then their y slopes), or 0 where src[j] < 0 (padding).

@@ -53,6 +53,8 @@ struct fwr_plan {
     fwr::DevTables<double> f64;
     // 256^2 grids: per-CTA global scratch of the slab kernel
     float2* d_scratch = nullptr;
+    // DFT-as-GEMM transform on 128^2 / 256^2 grids: operands and chunk buffers
+    void* d_dftws = nullptr;
     int scratch_ctas = 0;
     // host-path staging
     float* d_stage_in = nullptr;

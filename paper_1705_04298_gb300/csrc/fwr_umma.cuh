@@ -352,7 +352,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
     fence_before();
     __syncthreads();
-    if (*abort && threadIdx.x == 0) atomicExch(status, 2);
+    if (*abort && threadIdx.x == 0) atomicOr(status, 2);
     if (warp == 0) {
         fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(C::TMEM_COLS)

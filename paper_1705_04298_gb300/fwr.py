@@ -163,7 +163,9 @@ class Plan:
         self.periodic = mode
 
     def set_transform(self, mode):
-        """TRANSFORM_FFT (default) or TRANSFORM_DFT_BF16X3 (tensor-core split-BF16 DFT, N = 32/64)."""
+        """TRANSFORM_FFT (default) or TRANSFORM_DFT_BF16X3 (tensor-core split-BF16
+        DFT: per-frame products for N = 32/64, batched tcgen05 GEMMs for N =
+        128/256, whose workspace this call allocates)."""
         _check(self._lib.fwr_plan_set_option(self._h, OPT_TRANSFORM, float(mode)), "fwr_plan_set_option")
         self.transform = mode
 

@@ -1,5 +1,6 @@
 """Precision variant: 2-D transforms as dense DFT products on the tensor cores
-with split-BF16 operands (FWR_TRANSFORM_DFT_BF16X3, grids 32^2 and 64^2).
+with split-BF16 operands (FWR_TRANSFORM_DFT_BF16X3): per-frame mma.sync
+products for 32^2 and 64^2 grids, batched tcgen05 GEMMs for 128^2 and 256^2.
 The transform is checked against numpy's FFT, and whole reconstructions with
 it against the FP64 oracle; the measured errors are printed (pytest -s) and
 bounded here. A BF16 pair keeps 16 significant bits, so about 1e-5 per
@@ -65,8 +66,53 @@ def test_reconstruction_with_tensor_core_dft(fwr, n, pad, k, filt):
     assert worst < 1e-3
 
 
+@pytest.mark.parametrize("n,pad,k,filt,periodic", [(40, 3.2, 10, "wiener", 0), (40, 3.2, 2, "lsq", 1),
+                                                    (40, 3.2, 0, "lsq", 2), (80, 3.2, 5, "lsq", 0),
+                                                    (100, 2.0, 1, "wiener", 0)])
+def test_batched_tensor_core_dft_reconstruction(fwr, n, pad, k, filt, periodic):
+    """128^2 and 256^2 through the batched tcgen05 GEMMs against the FP64
+    oracle, every periodic mode. About 1e-5 per transform (16 significant
+    bits per split operand, FP32 sums over 6N terms); measured 6e-6 .. 1.7e-5."""
+    r0p, L0p = synth.pitch_units(n, 0.15, 25.0)
+    sig = 0.05
+    F = 2
+    sl, _, mask = synth.batch(n, F, 700 + n + k, sig)
+    plan = fwr.Plan(mask, pad, fwr.WIENER if filt == "wiener" else fwr.LSQ, sig ** 2, r0p, L0p)
+    plan.set_periodic(periodic)
+    plan.set_transform(fwr.TRANSFORM_DFT_BF16X3)
+    ph = plan.reconstruct(torch.tensor(sl, dtype=torch.float32, device="cuda"), k).cpu().numpy()
+    assert plan.status() == "FWR_OK"
+    worst = 0.0
+    for f in range(F):
+        ref, _ = oracle.reconstruct(sl[f], mask, pad, k,
+                                    oracle.FILTER_WIENER if filt == "wiener" else oracle.FILTER_LSQ,
+                                    sig ** 2, r0p, L0p, periodic)
+        worst = max(worst, rel_rms(ph[f], ref))
+    print("batched split-BF16 DFT n=%d N=%d k=%d periodic=%d: relative phase rms %.2e"
+          % (n, plan.N, k, periodic, worst))
+    assert worst < 1e-4
+
+
+def test_batched_tensor_core_dft_chunks_and_limits(fwr):
+    """More frames than one chunk (128 at 256^2): the second chunk's frames
+    match the first chunk's for identical inputs; ext_out is refused."""
+    n = 80
+    sl, _, mask = synth.batch(n, 2, 901, 0.05)
+    plan = fwr.Plan(mask, 3.2, fwr.LSQ)
+    plan.set_transform(fwr.TRANSFORM_DFT_BF16X3)
+    s = torch.tensor(sl, dtype=torch.float32, device="cuda").repeat(65, 1, 1, 1)  # 130 frames
+    ph = plan.reconstruct(s, 3)
+    assert plan.status() == "FWR_OK"
+    assert torch.equal(ph[0], ph[128]) and torch.equal(ph[1], ph[129])
+    assert torch.isfinite(ph).all()
+    with pytest.raises(fwr.FwrError) as e:
+        plan.reconstruct(s[:2], 3, ext_out=torch.empty((2, 2, 256, 256), device="cuda"))
+    assert e.value.code == 2
+
+
 def test_transform_option_limits(fwr):
-    plan = fwr.Plan(synth.pupil_mask(40), 3.2, fwr.LSQ)  # 128^2
+    plan = fwr.Plan(synth.pupil_mask(12), 1.25, fwr.LSQ)  # 16^2: no tensor-core DFT
+    assert plan.N == 16
     with pytest.raises(fwr.FwrError) as e:
         plan.set_transform(fwr.TRANSFORM_DFT_BF16X3)
     assert e.value.code == 2
