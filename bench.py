@@ -379,6 +379,24 @@ def learned_measurements(fwr, torch, flush):
     return res
 
 
+def learned_summary(extras):
+    """The warm start that meets the residual of ten plain iterations (within
+    1 %) with one iteration, against those ten plain iterations."""
+    if not extras or "learned_warm_start_40x40_128grid" not in extras:
+        return None
+    L = extras["learned_warm_start_40x40_128grid"]
+    lin = [k for k in L if k.startswith("linear_r")][0]
+    v, p10 = L[lin]["k1"], L["plain"]["k10"]
+    return {"path": "%s warm start + 1 Gerchberg iteration (fwr_linws_reconstruct, CUDA graph)" % lin,
+            "residual_rad": v["residual_rad"], "plain_k10_residual_rad": p10["residual_rad"],
+            "residual_vs_plain_k10": v["residual_vs_plain_k10"],
+            "frames_per_s": v["graph_frames_per_s"], "plain_k10_frames_per_s": p10["frames_per_s"],
+            "speedup_vs_plain_k10": v["graph_speedup_vs_plain_k10"],
+            "speedup_direct_call": v["speedup_vs_plain_k10"],
+            "unet_k1_residual_rad": L["unet"]["k1"]["residual_rad"],
+            "unet_k1_speedup_vs_plain_k10": L["unet"]["k1"]["speedup_vs_plain_k10"]}
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -539,6 +557,7 @@ def main():
                          "source_hash": src},
             "e2e": {"value": FRAMES * world / (e2e_step / 1000.0), "unit": "frames/s",
                     "h2d_bytes_per_step": int(sh.numel() * 4), "d2h_bytes_per_step": int(ph_host.numel() * 4)},
+            "learned_vs_plain": learned_summary(extras),
             "gpu_launches": gpu_launches,
             "clocks": clk,
             "cpu_baseline": cpu_base,
