@@ -289,11 +289,15 @@ __device__ __forceinline__ bool slab_frame(const SlabCtx& c, const Tables<float>
             }
             __syncthreads();
             // Algorithm 1 step 4 (and the embedding): measurement in the pupil
+            // the slope loads do not depend on the mask (every address is in
+            // the frame), so unrolled iterations keep several L2 reads in flight
             const int i0 = max(0, m0 - off), i1 = min(n, m0 + SL - off);
-            for (int c = tid; c < (i1 - i0) * n; c += SNT) {
+            const int cnt = (i1 - i0) * n;
+#pragma unroll 4
+            for (int c = tid; c < cnt; c += SNT) {
                 const int i = i0 + c / n, j = c % n;
+                const float vx = __ldg(sl + i * n + j), vy = __ldg(sl + nn + i * n + j);
                 if (mask[i * n + j]) {
-                    const float vx = sl[i * n + j], vy = sl[nn + i * n + j];
                     if (it < 0) finite &= isfinite(vx) && isfinite(vy);
                     Lb[(off + i - m0) * SLS + off + j] = make_float2(vx, vy);
                 }
