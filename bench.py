@@ -404,6 +404,27 @@ def dist_env():
     return rank, world, local
 
 
+def rank_seed0(rank):
+    """First frame seed of a rank: ranks reconstruct disjoint seeded batches
+    (weak scaling, no collective on the data path)."""
+    return SEED0 + rank * FRAMES
+
+
+def max_over_ranks(x, dist, device):
+    """The largest value of x over the ranks (the slowest rank sets the job's
+    time); x itself without a process group."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
+def whole_job_frames_per_s(frames_per_rank, world, ms_per_step):
+    return frames_per_rank * world / (ms_per_step / 1000.0)
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -466,7 +487,7 @@ def main():
 
     from paper_1705_04298_gb300 import fwr, synth
     k = args.iters
-    sl, _, mask = synth.batch(N_LENSLETS, FRAMES, SEED0 + rank * FRAMES, SIGMA, R0, L0)
+    sl, _, mask = synth.batch(N_LENSLETS, FRAMES, rank_seed0(rank), SIGMA, R0, L0)
     r0p, L0p = synth.pitch_units(N_LENSLETS, R0, L0)
     plan = fwr.Plan(mask, PAD, fwr.WIENER, SIGMA ** 2, r0p, L0p)
     N = plan.N
@@ -500,13 +521,9 @@ def main():
     barrier()
     clk = clocks.stop()
     gpu_launches = args.steps  # one fused kernel launch per step
-    total_ms = sum(times)
-    if dist is not None:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = t.item()
+    total_ms = max_over_ranks(sum(times), dist, "cuda")
     ms_per_step = total_ms / args.steps
-    value = FRAMES * world / (ms_per_step / 1000.0)
+    value = whole_job_frames_per_s(FRAMES, world, ms_per_step)
 
     # end to end through the host entry point: H2D slopes, kernel, D2H phase
     sh = torch.tensor(sl, dtype=torch.float32).pin_memory()
@@ -524,11 +541,7 @@ def main():
         plan.reconstruct_host(sh, k, ph_host)
         torch.cuda.synchronize()
         e2e_ms.append(1000.0 * (time.perf_counter() - t0))
-    e2e_step = statistics.median(e2e_ms)
-    if dist is not None:
-        t = torch.tensor([e2e_step], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_step = t.item()
+    e2e_step = max_over_ranks(statistics.median(e2e_ms), dist, "cuda")
 
     extras = None
     if rank == 0 and not args.no_extras:
