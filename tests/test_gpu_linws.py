@@ -1,9 +1,9 @@
 """The tcgen05 BF16 GEMM against an FP64 reference of the same BF16 inputs,
 and the linear warm start built on it: its extension operator against the
 oracle, its forward against an FP64 evaluation of the same BF16 factors, and
-the reconstruction it starts (full rank: k = 1 reproduces k = 11; the default
-rank on the 40 x 40 workload: within 1 % of the residual of 10 plain
-iterations)."""
+the reconstruction it starts (full rank, fitted to the extension: k = 1
+reproduces k = 11; the default phase-weighted rank on the 40 x 40 workload:
+within 1 % of the residual of 10 plain iterations)."""
 
 import numpy as np
 import pytest
@@ -100,7 +100,7 @@ def test_full_rank_warm_start_reproduces_eleven_iterations(fwr):
     n, plan, mask = small_setup(fwr)
     K = 2 * plan.valid_count
     r = (K + 127) // 128 * 128
-    ws, E = linws.build(fwr, plan, mask, rank=r, max_batch=64, frames=1024)
+    ws, E = linws.build(fwr, plan, mask, rank=r, max_batch=64, frames=1024, weight="extension")
     sl, _, _ = synth.batch(n, 64, 900, 0.05)
     s = torch.tensor(sl, dtype=torch.float32, device="cuda")
     x0 = ws.forward(s)
