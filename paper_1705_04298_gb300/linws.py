@@ -129,14 +129,15 @@ def fit_phase(E, P, X, rank):
     reconstructed phase rather than of the extension: with X = Q R and the
     SVD R P = U S Z^T, the rank-r optimum of ||X P - X A V^T L^T|| (L the map
     from the warm start to P) is Q U_r S_r Z_r^T; it is reached by A = R^-1
-    U_r S_r and V = E^T (Z_r^T P^+)^T, which keeps the warm start in the row
-    space of E."""
+    U_r S_r (minimum norm when there are fewer frames than slopes) and V =
+    E^T (Z_r^T P^+)^T, which keeps the warm start in the row space of E."""
     r = int(rank)
     R = np.linalg.qr(np.asarray(X, dtype=np.float64), mode="r")
     U, S, Zt = np.linalg.svd(R @ P, full_matrices=False)
     keep = min(r, len(S))
     A = np.zeros((E.shape[0], r))
-    A[:, :keep] = np.linalg.solve(R, U[:, :keep] * S[:keep])
+    # R is square (more frames than slopes) or wide: the minimum-norm solution of R A = U_r S_r
+    A[:, :keep] = np.linalg.lstsq(R, U[:, :keep] * S[:keep], rcond=None)[0]
     Bt = Zt[:keep] @ np.linalg.pinv(P, rcond=1e-10)       # keep x K
     V = np.zeros((E.shape[1], r))
     V[:, :keep] = E.T @ Bt.T

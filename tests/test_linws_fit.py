@@ -53,7 +53,11 @@ def test_phase_fit_reaches_the_phase_optimum():
     E = rng.standard_normal((K, M))
     L = rng.standard_normal((M, C)) * np.exp(-np.arange(C) / 8.0)
     P = E @ L
-    X = rng.standard_normal((80, K))
+    for frames in (80, 20):   # more and fewer frames than slopes
+        _check_phase_fit(E, L, P, rng.standard_normal((frames, K)))
+
+
+def _check_phase_fit(E, L, P, X):
     S = np.linalg.svd(X @ P, compute_uv=False)
     for r in (2, 5, 12):
         A, V = linws.fit_phase(E, P, X, r)
