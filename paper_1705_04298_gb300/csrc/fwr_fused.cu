@@ -44,12 +44,10 @@ fused_fft2_kernel(const float2* in, float2* out, int F, const float2* twg) {
     extern __shared__ __align__(16) unsigned char smem[];
     float2* Z = reinterpret_cast<float2*>(smem + L::z);
     float2* tw = reinterpret_cast<float2*>(smem + L::tw);
-    float2* tw1 = reinterpret_cast<float2*>(smem + L::tw1);
     float2* tw2 = reinterpret_cast<float2*>(smem + L::tw2);
     const int tid = threadIdx.x;
     for (int i = tid; i < N; i += NT) tw[i] = twg[i];
     __syncthreads();
-    for (int i = tid; i < 4 * R; i += NT) tw1[i] = tw[(i & 3) * (i >> 2)];
     for (int i = tid; i < 3 * R; i += NT) tw2[i] = tw[(i % R) * (1 + i / R)];
     int r, n2;
     row_role<N>(tid, r, n2);
@@ -67,11 +65,9 @@ fused_fft2_kernel(const float2* in, float2* out, int F, const float2* twg) {
             for (int n1 = 0; n1 < R; ++n1) x[n1] = rowp[4 * n1];
             dft_reg<R, false>(x);
 #pragma unroll
-            for (int k1 = 1; k1 < R; ++k1) x[k1] = twiddle<false>(x[k1], tw1[k1 * 4 + n2]);
-#pragma unroll
             for (int k1 = 0; k1 < R; ++k1) rowp[4 * k1] = x[k1];
             __syncthreads();
-            pass2<false, N>(Z, tw2);
+            pass2<false, N>(Z, tw, tw2);
             __syncthreads();
 #pragma unroll
             for (int m2 = 0; m2 < R; ++m2) x[m2] = colp[S * m2];
@@ -95,12 +91,10 @@ fused_fft2_kernel(const float2* in, float2* out, int F, const float2* twg) {
 #pragma unroll
             for (int m2 = 0; m2 < R; ++m2) colp[S * m2] = x[m2];
             __syncthreads();
-            pass2<true, N>(Z, tw2);
+            pass2<true, N>(Z, tw, tw2);
             __syncthreads();
 #pragma unroll
             for (int k1 = 0; k1 < R; ++k1) x[k1] = rowp[4 * k1];
-#pragma unroll
-            for (int k1 = 1; k1 < R; ++k1) x[k1] = twiddle<true>(x[k1], tw1[k1 * 4 + n2]);
             dft_reg<R, true>(x);
 #pragma unroll
             for (int n1 = 0; n1 < R; ++n1) rowp[4 * n1] = x[n1];

@@ -11,9 +11,9 @@
 // measured slopes and written for the phase only.
 //
 // 2-D FFT in three register passes (N = 4R):
-//   P1  rows, R-point DFT over n1 of elements 4 n1 + n2, twiddle w_N^(n2 k1)
-//   P2  rows 4-point DFT over n2  x  columns 4-point DFT over m1 of rows
-//       R m1 + m2, column twiddle w_N^(m2 q1)
+//   P1  rows, R-point DFT over n1 of elements 4 n1 + n2
+//   P2  row twiddle w_N^(n2 k1), rows 4-point DFT over n2  x  columns 4-point
+//       DFT over m1 of rows R m1 + m2, column twiddle w_N^(m2 q1)
 //   P3  columns, R-point DFT over m2
 // Each pass writes back to the cells it read, so the spectrum ends in a
 // digit-permuted layout: bin (ky, kx) sits at row R (ky mod 4) + ky / 4 and
@@ -61,8 +61,7 @@ struct Layout {
     static constexpr size_t z = 0;
     static constexpr size_t xpart = z + size_t(N) * S * sizeof(V);
     static constexpr size_t tw = xpart + size_t(4 * N) * sizeof(T);
-    static constexpr size_t tw1 = tw + size_t(N) * sizeof(V);
-    static constexpr size_t tw2 = tw1 + size_t(4 * R) * sizeof(V);
+    static constexpr size_t tw2 = tw + size_t(N) * sizeof(V);
     static constexpr size_t a = tw2 + size_t(3 * R) * sizeof(V);
     static constexpr size_t t = a + size_t(N) * sizeof(V);
     static constexpr size_t pt = t + size_t(N) * sizeof(V);
@@ -143,9 +142,12 @@ __device__ __forceinline__ V twiddle(V x, V w) {
 }
 
 // P2 in either direction over all R*R tasks (row radix-4 x column radix-4).
-// Task (m2, k1) owns rows R a + m2 and columns 4 k1 + b, a, b = 0..3.
+// Task (m2, k1) owns rows R a + m2 and columns 4 k1 + b, a, b = 0..3. The row
+// twiddle w_N^(b k1) between P1 and the row radix-4 is applied here, on the
+// way in (forward) or out (inverse): three twiddles per task, the same for a
+// whole warp, instead of R - 1 per P1 row task.
 template <bool INV, int N, typename V>
-__device__ __forceinline__ void pass2(V* Z, const V* tw2) {
+__device__ __forceinline__ void pass2(V* Z, const V* tw, const V* tw2) {
     constexpr int R = N / 4, S = N + 2, NT = 4 * N, TASKS = R * R, PER = (TASKS + NT - 1) / NT;
 #pragma unroll
     for (int i = 0; i < PER; ++i) {
@@ -156,10 +158,17 @@ __device__ __forceinline__ void pass2(V* Z, const V* tw2) {
         V x[4][4];
 #pragma unroll
         for (int a = 0; a < 4; ++a) load4(base + R * S * a, x[a]);
-        if (!INV) {
-            // rows: 4-point DFT over n2 (second index)
+        V wr[3];
 #pragma unroll
-            for (int a = 0; a < 4; ++a) dft_reg<4, false>(x[a]);
+        for (int b = 1; b < 4; ++b) wr[b - 1] = tw[b * k1];
+        if (!INV) {
+            // rows: twiddle w_N^(b k1), then 4-point DFT over n2 (second index)
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+#pragma unroll
+                for (int b = 1; b < 4; ++b) x[a][b] = twiddle<false>(x[a][b], wr[b - 1]);
+                dft_reg<4, false>(x[a]);
+            }
             // columns: 4-point DFT over m1 (first index), then w_N^(m2 q1)
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
@@ -189,7 +198,11 @@ __device__ __forceinline__ void pass2(V* Z, const V* tw2) {
                 for (int a = 0; a < 4; ++a) x[a][b] = c[a];
             }
 #pragma unroll
-            for (int a = 0; a < 4; ++a) dft_reg<4, true>(x[a]);
+            for (int a = 0; a < 4; ++a) {
+                dft_reg<4, true>(x[a]);
+#pragma unroll
+                for (int b = 1; b < 4; ++b) x[a][b] = twiddle<true>(x[a][b], wr[b - 1]);
+            }
         }
 #pragma unroll
         for (int a = 0; a < 4; ++a) store4c(base + R * S * a, x[a]);
@@ -206,7 +219,6 @@ struct FusedCtx {
     V* Z;
     T* xpart;
     V* tw;
-    V* tw1;
     V* tw2;
     V* A;
     V* Tt;
@@ -242,7 +254,6 @@ __device__ __forceinline__ void fused_setup(FusedCtx<T, N>& c, unsigned char* sm
     V* Z = c.Z = reinterpret_cast<V*>(smem + L::z);
     c.xpart = reinterpret_cast<T*>(smem + L::xpart);
     V* tw = c.tw = reinterpret_cast<V*>(smem + L::tw);
-    V* tw1 = c.tw1 = reinterpret_cast<V*>(smem + L::tw1);
     V* tw2 = c.tw2 = reinterpret_cast<V*>(smem + L::tw2);
     V* A = c.A = reinterpret_cast<V*>(smem + L::a);
     V* Tt = c.Tt = reinterpret_cast<V*>(smem + L::t);
@@ -272,7 +283,6 @@ __device__ __forceinline__ void fused_setup(FusedCtx<T, N>& c, unsigned char* sm
         if (wf) wf[i] = tab.wfin[src];
     }
     __syncthreads();
-    for (int i = tid; i < 4 * R; i += NT) tw1[i] = tw[(i & 3) * (i >> 2)];
     for (int i = tid; i < 3 * R; i += NT) tw2[i] = tw[(i % R) * (1 + i / R)];
 
     // Row stage: row r, columns 4 n1 + n2 (row_role). Column stage: storage
@@ -341,7 +351,6 @@ __device__ __forceinline__ bool fused_frame(const FusedCtx<T, N>& c, const T* sl
     const int tid = threadIdx.x;
     V* const Z = c.Z;
     T* const xpart = c.xpart;
-    const V* const tw1 = c.tw1;
     const V* const tw2 = c.tw2;
     const V* const A = c.A;
     const V* const Tt = c.Tt;
@@ -355,7 +364,7 @@ __device__ __forceinline__ bool fused_frame(const FusedCtx<T, N>& c, const T* sl
     const V* const s0row = c.s0row;
     const unsigned pmask = c.pmask;
     const V Ax = c.Ax, Tx = c.Tx;
-    const T pux = c.pux, puy = c.puy, a2u = c.a2u, t2u = c.t2u;
+    const T pux = c.pux, puy = c.puy, ha2u = T(0.5) * c.a2u, ht2u = T(0.5) * c.t2u;
     const T* const ptv = c.ptv;
     const V* const twv = c.twv;
     const T* const iop = c.iop;
@@ -450,15 +459,13 @@ __device__ __forceinline__ bool fused_frame(const FusedCtx<T, N>& c, const T* sl
             if (!phase) break;
         }
 
-        // ---- P1 forward: rows, R-point DFT over n1, twiddle w^(n2 k1)
+        // ---- P1 forward: rows, R-point DFT over n1 (its twiddle is applied in P2)
         dft_reg<R, false>(x);
-#pragma unroll
-        for (int k1 = 1; k1 < R; ++k1) x[k1] = twiddle<false>(x[k1], tw1[k1 * 4 + n2]);
 #pragma unroll
         for (int k1 = 0; k1 < R; ++k1) rowp[4 * k1] = x[k1];
         __syncthreads();
         // ---- P2 forward
-        pass2<false, N>(Z, tw2);
+        pass2<false, N>(Z, c.tw, tw2);
         __syncthreads();
         // ---- P3 forward: columns, R-point DFT over m2; bins stay in registers
 #pragma unroll
@@ -495,10 +502,15 @@ __device__ __forceinline__ bool fused_frame(const FusedCtx<T, N>& c, const T* sl
                 const T w = lo ? iop[4 * N * q2] : ion[-4 * N * q2];
                 const auto pv = load_pt(ptv + 16 * q2);
                 const T pvx = pv.x, pvy = pv.y, a2v = pv.z, t2v = pv.w;
-                const T Px = pux * pvx + puy * pvy, Py = puy * pvx - pux * pvy;
-                const T g2 = a2u * t2v + t2u * a2v, dg = a2u * t2v - t2u * a2v;
-                const T al = w * (half * g2 + Py), bx = half * w * dg, by = w * Px;
-                x[q2] = mk(al * z1.x + bx * z2c.x - by * z2c.y, al * z1.y + bx * z2c.y + by * z2c.x);
+                // alpha = w a, beta = w (b + i c): a = |G|^2/2 + Im P,
+                // b = (|Gx|^2 - |Gy|^2)/2, c = Re P; w scales the combination
+                const T Py = puy * pvx - pux * pvy;
+                const T ca = ha2u * t2v + (ht2u * a2v + Py);
+                const T cb = ha2u * t2v - ht2u * a2v;
+                const T cc = pux * pvx + puy * pvy;
+                const T yx = ca * z1.x + cb * z2c.x - cc * z2c.y;
+                const T yy = ca * z1.y + cb * z2c.y + cc * z2c.x;
+                x[q2] = mk(w * yx, w * yy);
             } else {
                 // Eq. 2: phi = Rx Sx + Ry Sy with 2 Sx = z1 + conj z2, 2 Sy = (z1 - conj z2) / i
                 const int ky = q1 + 4 * q2;
@@ -519,13 +531,11 @@ __device__ __forceinline__ bool fused_frame(const FusedCtx<T, N>& c, const T* sl
         for (int m2 = 0; m2 < R; ++m2) colp[S * m2] = x[m2];
         __syncthreads();
         // ---- P2 inverse
-        pass2<true, N>(Z, tw2);
+        pass2<true, N>(Z, c.tw, tw2);
         __syncthreads();
         // ---- P1 inverse
 #pragma unroll
         for (int k1 = 0; k1 < R; ++k1) x[k1] = rowp[4 * k1];
-#pragma unroll
-        for (int k1 = 1; k1 < R; ++k1) x[k1] = twiddle<true>(x[k1], tw1[k1 * 4 + n2]);
         dft_reg<R, true>(x);
 
         if (!final) {
