@@ -38,7 +38,9 @@
 //   * the y part of Eq. PC is applied in the frequency domain: setting the
 //     last row of y slopes to minus the column sums adds
 //     -Sy(0, kx) e^{2 i pi ky / N} to Sy(ky, kx), a rank-1 correction built
-//     from the ky = 0 row of the spectrum.
+//     from the ky = 0 row of the spectrum. Along one column task's bins it is
+//     the P3 DFT of a single input value, so it is added to that input before
+//     P3 (the ky = 0 bins are summed from the q1 = 0 inputs first).
 
 namespace {
 
@@ -470,32 +472,42 @@ __device__ __forceinline__ bool fused_frame(const FusedCtx<T, N>& c, const T* sl
         // ---- P3 forward: columns, R-point DFT over m2; bins stay in registers
 #pragma unroll
         for (int m2 = 0; m2 < R; ++m2) x[m2] = colp[S * m2];
+        if (fill) {
+            // y part of Eq. PC: the rank-1 correction -i Sy(0,kx) e^{2 i pi ky / N}
+            // of every bin (ky = q1 + 4 q2) is the R-point DFT of one value,
+            // d = -i Sy(0,kx) e^{2 i pi q1 / N}, added at m2 = R - 1. Sy(0,kx) =
+            // (Z(0,kx) - conj Z(0,-kx)) / (2i) needs the ky = 0 bins, i.e. the
+            // sums of the q1 = 0 inputs, published through xpart.
+            V* const dc = reinterpret_cast<V*>(xpart);
+            if (q1 == 0) {
+                V t[R];
+#pragma unroll
+                for (int m2 = 0; m2 < R; ++m2) t[m2] = x[m2];
+#pragma unroll
+                for (int h = R / 2; h >= 1; h /= 2)
+#pragma unroll
+                    for (int i = 0; i < h; ++i) t[i] = cadd(t[i], t[i + h]);
+                dc[gam] = t[0];
+            }
+            __syncthreads();
+            const V z0 = dc[gam], z0p = dc[gamp];
+            const V ey = mk(half * (z0.y + z0p.y), half * (z0p.x - z0.x));
+            const V tq = twv[0];
+            const V c0 = cmul(ey, mk(tq.x, -tq.y));
+            x[R - 1] = mk(x[R - 1].x + c0.y, x[R - 1].y - c0.x);
+        }
         dft_reg<R, false>(x);
 #pragma unroll
         for (int q2 = 0; q2 < R; ++q2) colp[S * q2] = x[q2];
         __syncthreads();
 
         // ---- spectral step on bins ky = q1 + 4 q2, kx
-        V ey = mk(T(0), T(0));
-        if (fill) {
-            // Sy(0, kx) = (Z(0,kx) - conj Z(0,-kx)) / (2i)
-            const V z0 = Z[gam], z0p = Z[gamp];
-            ey = mk(half * (z0.y + z0p.y), half * (z0p.x - z0.x));
-        }
 #pragma unroll
         for (int q2 = 0; q2 < R; ++q2) {
             // partner row of -ky: R q1n + q2n
             const V z2 = q1 == 0 ? partp[S * ((R - q2) & (R - 1))] : partp[S * (R - 1 - q2)];
-            V z1 = x[q2];
-            V z2c = mk(z2.x, -z2.y);
-            if (fill) {
-                // c = i * Sy(0,kx) * e^{2 i pi ky / N}
-                const V tk = twv[4 * q2];
-                const V c0 = cmul(ey, mk(tk.x, -tk.y));
-                const V cy = mk(-c0.y, c0.x);
-                z1 = csub(z1, cy);
-                z2c = cadd(z2c, cy);
-            }
+            const V z1 = x[q2];
+            const V z2c = mk(z2.x, -z2.y);
             const bool lo = 4 * q2 + q1 <= H;  // ky <= N/2: weight stored at (ky, kx)
             if (!final) {
                 // Algorithm 1 step 2: LSQ phase, slopes re-synthesised through G
