@@ -66,6 +66,8 @@ def flops_per_frame(N, k):
 TRAFFIC = {
     # ncu --set full, one k = 10 launch of 1000 frames: 12.985 MB read + 5.513 MB written
     "c4cdd161e6b0c782": 18497792,
+    # same capture after the P2 twiddles and the P3-input y fill: 12.994 MB + 5.890 MB
+    "97a3eb880aeb3f5d": 18883840,
 }
 
 
