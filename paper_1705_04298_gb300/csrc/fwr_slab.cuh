@@ -120,11 +120,12 @@ __device__ __forceinline__ int slab_partner(int s, int j) { return (s == 0 && j 
 }  // namespace
 
 // Shared-memory bytes of the slab path for n lenslets: the slab, the 1-D
-// tables, Sy(0, kx) per column pair, the spectral weights of the current
-// column slab (33 columns x 256 rows) and the mask.
+// tables (twiddles, a(u), T(u), the separable factors p(u)), Sy(0, kx) per
+// column pair, the spectral weights of the current column slab (33 columns x
+// 256 rows) and the mask.
 __host__ __device__ __forceinline__ size_t slab_layout_bytes(int n) {
-    return size_t(SL) * SLS * sizeof(float2) + 3 * size_t(SN) * sizeof(float2) + 33 * sizeof(float2) +
-           33 * size_t(SN) * sizeof(float) + ((size_t(n) * n + 15) & ~size_t(15));
+    return size_t(SL) * SLS * sizeof(float2) + 3 * size_t(SN) * sizeof(float2) + 4 * size_t(SN) * sizeof(float) +
+           33 * sizeof(float2) + 33 * size_t(SN) * sizeof(float) + ((size_t(n) * n + 15) & ~size_t(15));
 }
 
 // Per-CTA state of the slab path for one plan.
@@ -133,10 +134,12 @@ struct SlabCtx {
     float2* tw;
     float2* A;
     float2* Tt;
+    float* pt;
     float2* eyv;
     float* wts;
     uint8_t* mask;
     int n, off, nn, mode;
+    int pw;  // log2 of the lenslet count rounded up to a power of two
 };
 
 // Load a plan's 1-D tables and mask into shared memory; ends with a barrier.
@@ -146,19 +149,23 @@ __device__ __forceinline__ void slab_setup(SlabCtx& c, unsigned char* smem, cons
     c.tw = c.Lb + SL * SLS;
     c.A = c.tw + SN;
     c.Tt = c.A + SN;
-    c.eyv = c.Tt + SN;
+    c.pt = reinterpret_cast<float*>(c.Tt + SN);
+    c.eyv = reinterpret_cast<float2*>(c.pt + 4 * SN);
     c.wts = reinterpret_cast<float*>(c.eyv + 33);
     c.mask = reinterpret_cast<uint8_t*>(c.wts + 33 * SN);
     c.n = n;
     c.off = off;
     c.nn = n * n;
     c.mode = mode;
+    c.pw = 0;
+    while ((1 << c.pw) < n) ++c.pw;
     const int tid = threadIdx.x;
     for (int i = tid; i < SN; i += SNT) {
         c.tw[i] = tab.tw[i];
         c.A[i] = tab.A[i];
         c.Tt[i] = tab.Tt[i];
     }
+    for (int i = tid; i < 4 * SN; i += SNT) c.pt[i] = tab.pt[i];
     for (int i = tid; i < c.nn; i += SNT) c.mask[i] = mask_g[i];
     __syncthreads();
 }
@@ -167,6 +174,13 @@ __device__ __forceinline__ void slab_setup(SlabCtx& c, unsigned char* smem, cons
 // scratch area). sl: [2][n][n] slopes; ext: [2][N][N] warm start or nullptr;
 // phase: [N][N] output. Called by every thread; returns false in the threads
 // that saw a non-finite measured slope.
+//
+// Thread roles. Slab copies: a thread keeps one line (column slabs: line
+// tid mod 64, rows tid / 64 + 8 i) or one column (row slabs: column tid mod 256,
+// rows tid / 256 + 2 i), so its addresses advance by constant strides. Spectral
+// step: a thread keeps one frequency row ky = tid mod 256 (and its partner -ky)
+// and takes the lines j = tid / 256 + 2 i, so the ky factors stay in registers
+// and the kx factors are warp-uniform.
 __device__ __forceinline__ bool slab_frame(const SlabCtx& c, const Tables<float>& tab, const float* sl,
                                            const float* ext, float* phase, int iters, float2* G) {
     const int tid = threadIdx.x;
@@ -174,31 +188,43 @@ __device__ __forceinline__ bool slab_frame(const SlabCtx& c, const Tables<float>
     const float2* const tw = c.tw;
     const float2* const A = c.A;
     const float2* const Tt = c.Tt;
+    const float* const pt = c.pt;
     float2* const eyv = c.eyv;
     float* const wts = c.wts;
     const uint8_t* const mask = c.mask;
     const int n = c.n, off = c.off, nn = c.nn, mode = c.mode;
     bool finite = true;
+    // spectral roles: frequency row ky and its partner -ky
+    const int ky = tid & (SN - 1), kyn = (SN - ky) & (SN - 1);
+    const bool kylo = ky <= SH;
+    // column-slab copy roles: line jl, rows rb + 8 i
+    const int jl = tid & (SL - 1), rb = tid >> 6;
+    // row-slab copy roles: column cc, rows lb + 2 i
+    const int cc = tid & (SN - 1), lb = tid >> 8;
     // it = -1: embed; it = 0 .. iters-1: Gerchberg; it = iters: final
     for (int it = -1; it <= iters; ++it) {
         const bool final = it == iters;
         if (it >= 0) {
             // ------------------------------------------------ column phase
             const bool fill = mode == PERIODIC_BEFORE_EACH_FFT || (mode == PERIODIC_FINAL_ONLY && final);
+            // per-ky factors of the projection (LSQ) or of G (final filter)
+            const float4 pv = *reinterpret_cast<const float4*>(pt + 4 * ky);
+            const float2 Tky = Tt[ky], Aky = A[ky], twk = tw[ky];
             for (int s = 0; s < 4; ++s) {
-                for (int idx = tid; idx < SL * SN; idx += SNT) {
-                    const int m = idx / SL, j = idx % SL;
-                    cp_async8(Lb + j * SLS + m, G + m * SN + slab_col(s, j));
+                {
+                    const float2* src = G + slab_col(s, jl) + rb * SN;
+                    float2* dst = Lb + jl * SLS + rb;
+#pragma unroll 8
+                    for (int i = 0; i < SN / 8; ++i) cp_async8(dst + 8 * i, src + 8 * i * SN);
                 }
                 {
                     // spectral weights of the first-half columns: wts[j][ky] at
                     // (ky, kx) from the half-table (rows 0..N/2; (-ky, -kx) beyond)
-                    const float* wt = final ? tab.wfin : tab.iota;
+                    const float* wrow = (final ? tab.wfin : tab.iota) + (kylo ? ky : kyn) * SN;
                     const int nj = s == 0 ? 33 : 32;
-                    for (int idx = tid; idx < nj * SN; idx += SNT) {
-                        const int j = idx / SN, ky = idx % SN;
-                        const int kx = slab_col(s, j), kxn = (SN - kx) & (SN - 1);
-                        cp_async4(wts + idx, ky <= SH ? wt + ky * SN + kx : wt + ((SN - ky) & (SN - 1)) * SN + kxn);
+                    for (int j = lb; j < nj; j += 2) {
+                        const int kx = slab_col(s, j);
+                        cp_async4(wts + j * SN + ky, wrow + (kylo ? kx : (SN - kx) & (SN - 1)));
                     }
                 }
                 cp_wait_all();
@@ -212,48 +238,56 @@ __device__ __forceinline__ bool slab_frame(const SlabCtx& c, const Tables<float>
                     eyv[j] = make_float2(0.5f * (e0.y + e1.y), 0.5f * (e1.x - e0.x));
                 }
                 __syncthreads();
-                const int items = 32 * SN + (s == 0 ? SH + 1 : 0);
-                for (int q = tid; q < items; q += SNT) {
-                    int j, ky, pj;
-                    if (q < 32 * SN) {
-                        j = q / SN;
-                        ky = q % SN;
-                        pj = slab_partner(s, j);
-                        if (pj == j && ky > SH) continue;  // self-paired column: half the bins
-                    } else {
-                        j = 32;  // column 128 in slab 0, self-paired
-                        ky = q - 32 * SN;
-                        pj = 32;
-                    }
-                    const int kx = slab_col(s, j);
-                    const int kyn = (SN - ky) & (SN - 1);
-                    const float2 z1 = Lb[j * SLS + ky], z2 = Lb[pj * SLS + kyn];
-                    float2 sx = make_float2(0.5f * (z1.x + z2.x), 0.5f * (z1.y - z2.y));
-                    float2 sy = make_float2(0.5f * (z1.y + z2.y), 0.5f * (z2.x - z1.x));
+                // one (k, -k) pair per item: line j (kx) at row ky, partner line pj
+                // (-kx) at row -ky; lines 0..31, plus line 32 (column 128) in slab 0
+                const int jend = (s == 0 && tid <= SH) ? 34 : 32;
+                for (int j = lb; j < jend; j += 2) {
+                    const int jj = j < 32 ? j : 32;
+                    const int pj = jj < 32 ? slab_partner(s, jj) : 32;
+                    if (pj == jj && ky > SH) continue;  // self-paired column: half the rows
+                    const int kx = slab_col(s, jj);
+                    float2 z1 = Lb[jj * SLS + ky], z2 = Lb[pj * SLS + kyn];
                     if (fill) {
-                        // y part of Eq. PC: Sy(ky,kx) -= Sy(0,kx) e^{2 i pi ky / N}
-                        const float2 c = cmul(eyv[j], conjf2(tw[ky]));
-                        sy = make_float2(sy.x - c.x, sy.y - c.y);
+                        // y part of Eq. PC: Sy(ky,kx) -= Sy(0,kx) e^{2 i pi ky / N}, i.e.
+                        // Z(k) -= i c and Z(-k) -= i conj(c), c = Sy(0,kx) e^{2 i pi ky / N}
+                        const float2 c0 = cmul(eyv[jj], conjf2(twk));
+                        z1 = make_float2(z1.x + c0.y, z1.y - c0.x);
+                        z2 = make_float2(z2.x - c0.y, z2.y - c0.x);
                     }
-                    const float2 gx = cmul(A[kx], Tt[ky]);
-                    const float2 gy = cmul(Tt[kx], A[ky]);
-                    const float w = wts[j * SN + ky];
-                    float2 ph = cadd(cmulc(gx, sx), cmulc(gy, sy));
-                    ph = make_float2(ph.x * w, ph.y * w);
+                    const float w = wts[jj * SN + ky];
                     if (!final) {
-                        const float2 ox = cmul(gx, ph), oy = cmul(gy, ph);
-                        Lb[pj * SLS + kyn] = make_float2(ox.x + oy.y, oy.x - ox.y);
-                        Lb[j * SLS + ky] = make_float2(ox.x - oy.y, ox.y + oy.x);
+                        // Algorithm 1 step 2 for both bins: Z'(k) = w (a z1 + b conj z2),
+                        // Z'(-k) = w (a' z2 + b conj z1), a = |G|^2/2 + Im P, a' = |G|^2/2 - Im P,
+                        // b = (|Gx|^2 - |Gy|^2)/2 + i Re P, P = p(u) conj p(v)
+                        const float4 pu = *reinterpret_cast<const float4*>(pt + 4 * kx);
+                        const float Px = pu.x * pv.x + pu.y * pv.y, Py = pu.y * pv.x - pu.x * pv.y;
+                        const float h1 = 0.5f * pu.z * pv.w, h2 = 0.5f * pu.w * pv.z;
+                        const float g = h1 + h2, br = h1 - h2, bi = Px;
+                        const float a = g + Py, an = g - Py;
+                        const float2 o1 = make_float2(a * z1.x + br * z2.x + bi * z2.y, a * z1.y + bi * z2.x - br * z2.y);
+                        const float2 o2 = make_float2(an * z2.x + br * z1.x + bi * z1.y, an * z2.y + bi * z1.x - br * z1.y);
+                        Lb[pj * SLS + kyn] = make_float2(w * o2.x, w * o2.y);
+                        Lb[jj * SLS + ky] = make_float2(w * o1.x, w * o1.y);
                     } else {
+                        // Eq. 2 with the final filter: phi = w (conj(Gx) Sx + conj(Gy) Sy)
+                        const float2 z2c = conjf2(z2);
+                        const float2 sx = make_float2(0.5f * (z1.x + z2c.x), 0.5f * (z1.y + z2c.y));
+                        const float2 sy = make_float2(0.5f * (z1.y - z2c.y), 0.5f * (z2c.x - z1.x));
+                        const float2 gx = cmul(A[kx], Tky);
+                        const float2 gy = cmul(Tt[kx], Aky);
+                        float2 ph = cadd(cmulc(gx, sx), cmulc(gy, sy));
+                        ph = make_float2(ph.x * w, ph.y * w);
                         Lb[pj * SLS + kyn] = conjf2(ph);
-                        Lb[j * SLS + ky] = ph;
+                        Lb[jj * SLS + ky] = ph;
                     }
                 }
                 __syncthreads();
                 line_fft<true>(Lb, tw);
-                for (int idx = tid; idx < SL * SN; idx += SNT) {
-                    const int m = idx / SL, j = idx % SL;
-                    __stcg(G + m * SN + slab_col(s, j), Lb[j * SLS + m]);
+                {
+                    float2* dst = G + slab_col(s, jl) + rb * SN;
+                    const float2* src = Lb + jl * SLS + rb;
+#pragma unroll 8
+                    for (int i = 0; i < SN / 8; ++i) __stcg(dst + 8 * i * SN, src[8 * i]);
                 }
                 __syncthreads();
             }
@@ -264,25 +298,25 @@ __device__ __forceinline__ bool slab_frame(const SlabCtx& c, const Tables<float>
         for (int b = 0; b < 4; ++b) {
             const int m0 = SL * b;
             if (it < 0) {
-                for (int idx = tid; idx < SL * SN; idx += SNT) {
-                    const int l = idx / SN, c = idx % SN;
-                    const int g = (m0 + l) * SN + c;
-                    Lb[l * SLS + c] = ext ? make_float2(ext[g], ext[SN * SN + g]) : make_float2(0.f, 0.f);
+                for (int l = lb; l < SL; l += 2) {
+                    const int g = (m0 + l) * SN + cc;
+                    Lb[l * SLS + cc] = ext ? make_float2(ext[g], ext[SN * SN + g]) : make_float2(0.f, 0.f);
                 }
             } else {
-                for (int idx = tid; idx < SL * SN; idx += SNT) {
-                    const int l = idx / SN, c = idx % SN;
-                    cp_async8(Lb + l * SLS + c, G + (m0 + l) * SN + c);
+                {
+                    const float2* src = G + (m0 + lb) * SN + cc;
+                    float2* dst = Lb + lb * SLS + cc;
+#pragma unroll 8
+                    for (int i = 0; i < SL / 2; ++i) cp_async8(dst + 2 * i * SLS, src + 2 * i * SN);
                 }
                 cp_wait_all();
                 __syncthreads();
                 line_fft<true>(Lb, tw);
                 if (final) {
-                    float* ph = phase;
-                    for (int idx = tid; idx < SL * SN; idx += SNT) {
-                        const int l = idx / SN, c = idx % SN;
-                        __stcs(ph + (m0 + l) * SN + c, Lb[l * SLS + c].x);
-                    }
+                    float* ph = phase + (m0 + lb) * SN + cc;
+                    const float2* src = Lb + lb * SLS + cc;
+#pragma unroll 8
+                    for (int i = 0; i < SL / 2; ++i) __stcs(ph + 2 * i * SN, src[2 * i * SLS].x);
                     __syncthreads();
                     continue;
                 }
@@ -291,15 +325,17 @@ __device__ __forceinline__ bool slab_frame(const SlabCtx& c, const Tables<float>
             // Algorithm 1 step 4 (and the embedding): measurement in the pupil
             // the slope loads do not depend on the mask (every address is in
             // the frame), so unrolled iterations keep several L2 reads in flight
+            // (thread: lenslet column tid mod 2^pw, rows tid >> pw + steps of 512 >> pw)
             const int i0 = max(0, m0 - off), i1 = min(n, m0 + SL - off);
-            const int cnt = (i1 - i0) * n;
+            const int j = tid & ((1 << c.pw) - 1);
+            if (j < n) {
 #pragma unroll 4
-            for (int c = tid; c < cnt; c += SNT) {
-                const int i = i0 + c / n, j = c % n;
-                const float vx = __ldg(sl + i * n + j), vy = __ldg(sl + nn + i * n + j);
-                if (mask[i * n + j]) {
-                    if (it < 0) finite &= isfinite(vx) && isfinite(vy);
-                    Lb[(off + i - m0) * SLS + off + j] = make_float2(vx, vy);
+                for (int i = i0 + (tid >> c.pw); i < i1; i += SNT >> c.pw) {
+                    const float vx = __ldg(sl + i * n + j), vy = __ldg(sl + nn + i * n + j);
+                    if (mask[i * n + j]) {
+                        if (it < 0) finite &= isfinite(vx) && isfinite(vy);
+                        Lb[(off + i - m0) * SLS + off + j] = make_float2(vx, vy);
+                    }
                 }
             }
             __syncthreads();
@@ -315,9 +351,11 @@ __device__ __forceinline__ bool slab_frame(const SlabCtx& c, const Tables<float>
                 __syncthreads();
             }
             line_fft<false>(Lb, tw);
-            for (int idx = tid; idx < SL * SN; idx += SNT) {
-                const int l = idx / SN, c = idx % SN;
-                __stcg(G + (m0 + l) * SN + c, Lb[l * SLS + c]);
+            {
+                float2* dst = G + (m0 + lb) * SN + cc;
+                const float2* src = Lb + lb * SLS + cc;
+#pragma unroll 8
+                for (int i = 0; i < SL / 2; ++i) __stcg(dst + 2 * i * SN, src[2 * i * SLS]);
             }
             __syncthreads();
         }
