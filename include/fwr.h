@@ -173,15 +173,22 @@ fwr_status fwr_reconstruct_f64(fwr_plan* plan, const double* slopes_dev, const d
 /*
  * End-to-end FP32 call on HOST buffers: copies slopes_host
  * ([n_frames][2][n][n]) to plan-owned device staging, reconstructs and copies
- * the phase back to phase_host ([n_frames][N][N]), all on `stream`. The
- * staging grows on demand (cudaMalloc on the first call with a larger
- * n_frames; fwr_plan_reserve does it ahead). Returns after enqueueing; the
+ * the phase back to phase_host ([n_frames][N][N]), ordered on `stream`.
+ * The frames go in chunks of whole SM-waves (at least two, at most four
+ * chunks): the plan's two copy streams move chunk c + 1 in and chunk c - 1
+ * out while chunk c is reconstructed on `stream`, joined to `stream` by
+ * events, so work enqueued on `stream` afterwards sees the whole result.
+ * Host buffers should be pinned for the copies to overlap (pageable buffers
+ * give the same result without overlap). The staging grows on demand
+ * (cudaMalloc on the first call with a larger n_frames; fwr_plan_reserve does
+ * it ahead and creates the copy streams). Calls on one plan must not run
+ * concurrently from several host threads. Returns after enqueueing; the
  * caller synchronises `stream` before reading phase_host.
  */
 fwr_status fwr_reconstruct_host(fwr_plan* plan, const float* slopes_host, int n_frames, int iters,
                                 float* phase_host, void* stream);
 
-/* Pre-allocate host-path staging for n_frames frames. */
+/* Pre-allocate host-path staging for n_frames frames (and the copy streams). */
 fwr_status fwr_plan_reserve(fwr_plan* plan, int n_frames);
 
 /*

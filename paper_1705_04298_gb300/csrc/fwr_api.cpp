@@ -257,6 +257,10 @@ void fwr_plan_destroy(fwr_plan* p) {
     cudaFree(p->d_dftws);
     cudaFree(p->d_stage_in);
     cudaFree(p->d_stage_out);
+    if (p->s_h2d) cudaStreamDestroy(p->s_h2d);
+    if (p->s_d2h) cudaStreamDestroy(p->s_d2h);
+    for (cudaEvent_t ev : {p->ev_start, p->ev_in, p->ev_k, p->ev_done})
+        if (ev) cudaEventDestroy(ev);
     cudaSetDevice(prev);
     delete p;
 }
@@ -417,6 +421,19 @@ fwr_status fwr_reconstruct_f64(fwr_plan* p, const double* slopes, const double* 
 
 fwr_status fwr_plan_reserve(fwr_plan* p, int n_frames) {
     if (!p || n_frames < 0) return FWR_ERR_ARG;
+    if (!p->s_h2d) {
+        cudaError_t e;
+        if ((e = cudaStreamCreateWithFlags(&p->s_h2d, cudaStreamNonBlocking)) != cudaSuccess ||
+            (e = cudaStreamCreateWithFlags(&p->s_d2h, cudaStreamNonBlocking)) != cudaSuccess)
+            return cuda_fail(e, "cudaStreamCreate (host path)");
+        for (cudaEvent_t* ev : {&p->ev_start, &p->ev_in, &p->ev_k, &p->ev_done})
+            if ((e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming)) != cudaSuccess)
+                return cuda_fail(e, "cudaEventCreate (host path)");
+        int dev = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+            (e = cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+            return cuda_fail(e, "device attributes (host path)");
+    }
     if (n_frames <= p->stage_frames) return FWR_OK;
     cudaFree(p->d_stage_in);
     cudaFree(p->d_stage_out);
@@ -439,14 +456,44 @@ fwr_status fwr_reconstruct_host(fwr_plan* p, const float* slopes_host, int n_fra
     if (n_frames == 0) return FWR_OK;
     if ((st = fwr_plan_reserve(p, n_frames)) != FWR_OK) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const size_t in_b = size_t(n_frames) * 2 * p->n * p->n * sizeof(float);
-    const size_t out_b = size_t(n_frames) * p->N * p->N * sizeof(float);
-    cudaError_t e = cudaMemcpyAsync(p->d_stage_in, slopes_host, in_b, cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return cuda_fail(e, "H2D slopes");
-    st = fwr_reconstruct_ex(p, p->d_stage_in, nullptr, n_frames, iters, p->d_stage_out, nullptr, stream);
-    if (st != FWR_OK) return st;
-    e = cudaMemcpyAsync(phase_host, p->d_stage_out, out_b, cudaMemcpyDeviceToHost, s);
-    return e == cudaSuccess ? FWR_OK : cuda_fail(e, "D2H phase");
+    const size_t in_f = size_t(2) * p->n * p->n, out_f = size_t(p->N) * p->N;  // floats per frame
+    // Pipelined in chunks of whole waves of the persistent kernel (at least two
+    // SM-waves, at most four chunks): the H2D copy of chunk c + 1 and the D2H
+    // copy of chunk c - 1 run on the plan's copy streams while chunk c computes
+    // on `stream`; events order each chunk's copy -> kernel -> copy and join
+    // the copy streams back to `stream`.
+    const int wave = p->sms > 0 ? p->sms : 1;
+    int chunk = (n_frames + 3) / 4;
+    chunk = (chunk + wave - 1) / wave * wave;
+    if (chunk < 2 * wave) chunk = 2 * wave;
+    cudaError_t e;
+    if ((e = cudaEventRecord(p->ev_start, s)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(p->s_h2d, p->ev_start, 0)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(p->s_d2h, p->ev_start, 0)) != cudaSuccess)
+        return cuda_fail(e, "host path ordering");
+    for (int f0 = 0; f0 < n_frames; f0 += chunk) {
+        const int fc = n_frames - f0 < chunk ? n_frames - f0 : chunk;
+        float* din = p->d_stage_in + size_t(f0) * in_f;
+        float* dout = p->d_stage_out + size_t(f0) * out_f;
+        if ((e = cudaMemcpyAsync(din, slopes_host + size_t(f0) * in_f, size_t(fc) * in_f * sizeof(float),
+                                 cudaMemcpyHostToDevice, p->s_h2d)) != cudaSuccess)
+            return cuda_fail(e, "H2D slopes");
+        if ((e = cudaEventRecord(p->ev_in, p->s_h2d)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(s, p->ev_in, 0)) != cudaSuccess)
+            return cuda_fail(e, "host path ordering");
+        st = fwr_reconstruct_ex(p, din, nullptr, fc, iters, dout, nullptr, stream);
+        if (st != FWR_OK) return st;
+        if ((e = cudaEventRecord(p->ev_k, s)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(p->s_d2h, p->ev_k, 0)) != cudaSuccess)
+            return cuda_fail(e, "host path ordering");
+        if ((e = cudaMemcpyAsync(phase_host + size_t(f0) * out_f, dout, size_t(fc) * out_f * sizeof(float),
+                                 cudaMemcpyDeviceToHost, p->s_d2h)) != cudaSuccess)
+            return cuda_fail(e, "D2H phase");
+    }
+    if ((e = cudaEventRecord(p->ev_done, p->s_d2h)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(s, p->ev_done, 0)) != cudaSuccess)
+        return cuda_fail(e, "host path ordering");
+    return FWR_OK;
 }
 
 static fwr_status twiddles_for(int N, float2** out);

@@ -60,4 +60,9 @@ struct fwr_plan {
     float* d_stage_in = nullptr;
     float* d_stage_out = nullptr;
     int stage_frames = 0;
+    // host path: copy streams (H2D, D2H) and the events that join them to the
+    // caller's stream, created with the staging
+    cudaStream_t s_h2d = nullptr, s_d2h = nullptr;
+    cudaEvent_t ev_start = nullptr, ev_in = nullptr, ev_k = nullptr, ev_done = nullptr;
+    int sms = 0;
 };

@@ -234,7 +234,8 @@ class Plan:
     def reconstruct_host(self, slopes_host, iters, phase_host, stream=None):
         """End-to-end call on host tensors (pinned for asynchronous copies):
         slopes_host (F, 2, n, n) float32 CPU, phase_host (F, N, N) float32 CPU.
-        Enqueues H2D, the reconstruction and D2H on `stream`."""
+        Ordered on `stream`: the copies of later and earlier chunks overlap the
+        reconstruction of the current one on the plan's copy streams."""
         import torch
         F = slopes_host.shape[0]
         for t, shp, name in ((slopes_host, (F, 2, self.n, self.n), "slopes_host"),

@@ -231,6 +231,29 @@ def test_nonfinite_input_sets_status(fwr):
     assert plan.status() == "FWR_OK"  # read-and-clear
 
 
+@pytest.mark.parametrize("n,pad", [(40, 3.2), (80, 3.2)])
+def test_host_path_chunks_match_device_path(fwr, n, pad):
+    """The host entry point pipelines its copies in chunks of whole SM-waves
+    (several chunks and a partial last one here, on a side stream, two calls
+    back to back): bit-identical to the device entry point."""
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    F = 4 * sms + 37 if n == 40 else 2 * sms + 5
+    k = 2
+    sl, _, mask = synth.batch(n, F, 11, 0.05)
+    plan = make_plan(fwr, mask, pad, fwr.LSQ)
+    ref = plan.reconstruct(torch.tensor(sl, dtype=torch.float32, device="cuda"), k).cpu()
+    sh = torch.tensor(sl, dtype=torch.float32).pin_memory()
+    out1 = torch.full((F, plan.N, plan.N), float("nan"), dtype=torch.float32).pin_memory()
+    out2 = torch.full((F, plan.N, plan.N), float("nan"), dtype=torch.float32).pin_memory()
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        plan.reconstruct_host(sh, k, out1)
+        plan.reconstruct_host(sh, k, out2)
+    side.synchronize()
+    assert torch.equal(out1, ref)
+    assert torch.equal(out2, ref)
+
+
 def test_deterministic_and_host_path_identical(fwr):
     n, pad, k, F = 40, 3.2, 5, 64
     sl, _, mask = synth.batch(n, F, 3, 0.05)
