@@ -36,6 +36,7 @@ constexpr int SL = 64;         // lines per slab
 constexpr int SLS = SN + 1;    // line stride in shared memory
 constexpr int SNT = 512;       // threads per CTA
 constexpr int SH = SN / 2;
+constexpr int WS = 33;         // row stride of the spectral weights of a column slab
 
 __device__ __forceinline__ float2 conjf2(float2 a) { return make_float2(a.x, -a.y); }
 
@@ -121,11 +122,11 @@ __device__ __forceinline__ int slab_partner(int s, int j) { return (s == 0 && j 
 
 // Shared-memory bytes of the slab path for n lenslets: the slab, the 1-D
 // tables (twiddles, a(u), T(u), the separable factors p(u)), Sy(0, kx) per
-// column pair, the spectral weights of the current column slab (33 columns x
-// 256 rows) and the mask.
+// column pair, the spectral weights of the current column slab (256 rows x
+// 33 columns) and the mask.
 __host__ __device__ __forceinline__ size_t slab_layout_bytes(int n) {
     return size_t(SL) * SLS * sizeof(float2) + 3 * size_t(SN) * sizeof(float2) + 4 * size_t(SN) * sizeof(float) +
-           33 * sizeof(float2) + 33 * size_t(SN) * sizeof(float) + ((size_t(n) * n + 15) & ~size_t(15));
+           33 * sizeof(float2) + WS * size_t(SN) * sizeof(float) + ((size_t(n) * n + 15) & ~size_t(15));
 }
 
 // Per-CTA state of the slab path for one plan.
@@ -152,7 +153,7 @@ __device__ __forceinline__ void slab_setup(SlabCtx& c, unsigned char* smem, cons
     c.pt = reinterpret_cast<float*>(c.Tt + SN);
     c.eyv = reinterpret_cast<float2*>(c.pt + 4 * SN);
     c.wts = reinterpret_cast<float*>(c.eyv + 33);
-    c.mask = reinterpret_cast<uint8_t*>(c.wts + 33 * SN);
+    c.mask = reinterpret_cast<uint8_t*>(c.wts + WS * SN);
     c.n = n;
     c.off = off;
     c.nn = n * n;
@@ -196,7 +197,6 @@ __device__ __forceinline__ bool slab_frame(const SlabCtx& c, const Tables<float>
     bool finite = true;
     // spectral roles: frequency row ky and its partner -ky
     const int ky = tid & (SN - 1), kyn = (SN - ky) & (SN - 1);
-    const bool kylo = ky <= SH;
     // column-slab copy roles: line jl, rows rb + 8 i
     const int jl = tid & (SL - 1), rb = tid >> 6;
     // row-slab copy roles: column cc, rows lb + 2 i
@@ -218,14 +218,15 @@ __device__ __forceinline__ bool slab_frame(const SlabCtx& c, const Tables<float>
                     for (int i = 0; i < SN / 8; ++i) cp_async8(dst + 8 * i, src + 8 * i * SN);
                 }
                 {
-                    // spectral weights of the first-half columns: wts[j][ky] at
-                    // (ky, kx) from the half-table (rows 0..N/2; (-ky, -kx) beyond)
-                    const float* wrow = (final ? tab.wfin : tab.iota) + (kylo ? ky : kyn) * SN;
-                    const int nj = s == 0 ? 33 : 32;
-                    for (int j = lb; j < nj; j += 2) {
-                        const int kx = slab_col(s, j);
-                        cp_async4(wts + j * SN + ky, wrow + (kylo ? kx : (SN - kx) & (SN - 1)));
-                    }
+                    // spectral weights of the first-half columns: wts[ky][j] at
+                    // (ky, kx) from the half-table (rows 0..N/2; (-ky, -kx) beyond);
+                    // a warp reads 32 adjacent columns of one table row
+                    const float* wt = final ? tab.wfin : tab.iota;
+                    const int j = tid & 31, kx = slab_col(s, j), kxn = (SN - kx) & (SN - 1);
+                    for (int k = tid >> 5; k < SN; k += SNT / 32)
+                        cp_async4(wts + k * WS + j, wt + (k <= SH ? k * SN + kx : (SN - k) * SN + kxn));
+                    if (s == 0 && tid < SN)  // line 32: the self-paired column 128
+                        cp_async4(wts + tid * WS + 32, wt + (tid <= SH ? tid : SN - tid) * SN + SH);
                 }
                 cp_wait_all();
                 __syncthreads();
@@ -254,7 +255,7 @@ __device__ __forceinline__ bool slab_frame(const SlabCtx& c, const Tables<float>
                         z1 = make_float2(z1.x + c0.y, z1.y - c0.x);
                         z2 = make_float2(z2.x - c0.y, z2.y - c0.x);
                     }
-                    const float w = wts[jj * SN + ky];
+                    const float w = wts[ky * WS + jj];
                     if (!final) {
                         // Algorithm 1 step 2 for both bins: Z'(k) = w (a z1 + b conj z2),
                         // Z'(-k) = w (a' z2 + b conj z1), a = |G|^2/2 + Im P, a' = |G|^2/2 - Im P,
@@ -340,8 +341,10 @@ __device__ __forceinline__ bool slab_frame(const SlabCtx& c, const Tables<float>
             }
             __syncthreads();
             if (fill_next) {
-                // x part of Eq. PC: 8 lanes per row
-                const int l = tid >> 3, part = tid & 7;
+                // x part of Eq. PC: 8 lanes per row; a warp takes rows 8 apart so
+                // its lanes read .x words in distinct bank pairs
+                const int w = tid >> 5, lane = tid & 31;
+                const int l = 32 * (w >> 3) + (w & 7) + 8 * (lane >> 3), part = lane & 7;
                 float s = 0.f;
                 for (int c = part; c < SN - 1; c += 8) s += Lb[l * SLS + c].x;
                 s += __shfl_xor_sync(0xffffffffu, s, 1);
