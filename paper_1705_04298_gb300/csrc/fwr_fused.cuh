@@ -502,13 +502,16 @@ __device__ __forceinline__ bool fused_frame(const FusedCtx<T, N>& c, const T* sl
         __syncthreads();
 
         // ---- spectral step on bins ky = q1 + 4 q2, kx
+        // partner row of -ky: R q1n + q2n, q2n = R - 1 - q2 (q1 > 0) or R - q2 (q1 = 0, q2 > 0)
+        const V* const partq = q1 == 0 ? partp + S : partp;
 #pragma unroll
         for (int q2 = 0; q2 < R; ++q2) {
-            // partner row of -ky: R q1n + q2n
-            const V z2 = q1 == 0 ? partp[S * ((R - q2) & (R - 1))] : partp[S * (R - 1 - q2)];
+            const V z2 = q2 == 0 ? (q1 == 0 ? partp[0] : partp[S * (R - 1)]) : partq[S * (R - 1 - q2)];
             const V z1 = x[q2];
             const V z2c = mk(z2.x, -z2.y);
-            const bool lo = 4 * q2 + q1 <= H;  // ky <= N/2: weight stored at (ky, kx)
+            // ky = 4 q2 + q1 <= N/2: weight stored at (ky, kx); known at compile
+            // time except for q2 = N/8
+            const bool lo = q2 < R / 2 || (q2 == R / 2 && q1 == 0);
             if (!final) {
                 // Algorithm 1 step 2: LSQ phase, slopes re-synthesised through G
                 const T w = lo ? iop[4 * N * q2] : ion[-4 * N * q2];
