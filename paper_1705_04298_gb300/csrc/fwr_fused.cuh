@@ -427,11 +427,17 @@ __device__ __forceinline__ bool fused_frame(const FusedCtx<T, N>& c, const T* sl
         const bool fill = mode == PERIODIC_BEFORE_EACH_FFT || (mode == PERIODIC_FINAL_ONLY && final);
         if (fill) {
             // x part: last column of x slopes = -(sum of the other N-1 of its row)
-            T s = T(0);
+            // pairwise sum of the thread's R values (the n2 = 3 thread leaves
+            // out the last column)
+            T t[R];
 #pragma unroll
-            for (int n1 = 0; n1 < R; ++n1)
-                if (!(n1 == R - 1 && n2 == 3)) s += x[n1].x;
-            xpart[n2 * N + r] = s;
+            for (int n1 = 0; n1 < R; ++n1) t[n1] = x[n1].x;
+            if (n2 == 3) t[R - 1] = T(0);
+#pragma unroll
+            for (int h = R / 2; h >= 1; h /= 2)
+#pragma unroll
+                for (int i = 0; i < h; ++i) t[i] += t[i + h];
+            xpart[n2 * N + r] = t[0];
             __syncthreads();
             if (n2 == 3) x[R - 1].x = -(((xpart[r] + xpart[N + r]) + xpart[2 * N + r]) + xpart[3 * N + r]);
         }
@@ -554,10 +560,13 @@ __device__ __forceinline__ bool fused_frame(const FusedCtx<T, N>& c, const T* sl
         dft_reg<R, true>(x);
 
         if (!final) {
-            // Algorithm 1 step 4: measured slopes back in the pupil
+            // Algorithm 1 step 4: measured slopes back in the pupil (rows
+            // without pupil cells skip the loop, whole warps at a time)
+            if (pmask) {
 #pragma unroll
-            for (int n1 = 0; n1 < R; ++n1)
-                if (pmask & (1u << n1)) x[n1] = s0row[4 * n1];
+                for (int n1 = 0; n1 < R; ++n1)
+                    if (pmask & (1u << n1)) x[n1] = s0row[4 * n1];
+            }
         } else {
             // real phase out through shared memory: every thread has read its
             // row cells, the real parts go to compact rows (stride S values,
