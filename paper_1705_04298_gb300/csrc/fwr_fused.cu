@@ -22,6 +22,8 @@ fused_kernel(Params<T> p) {
     const int nn = p.n * p.n;
     bool finite = true;
     for (int f = blockIdx.x; f < p.F; f += gridDim.x) {
+        // the CTA's next frame's slopes into L2 while this one is worked
+        if (f + int(gridDim.x) < p.F) prefetch_l2(p.slopes + size_t(f + gridDim.x) * 2 * nn, 2 * nn * sizeof(T));
         finite &= fused_frame<T, N>(c, p.slopes + size_t(f) * 2 * nn,
                                     p.ext_init ? p.ext_init + size_t(f) * 2 * N * N : nullptr,
                                     p.ext_init_h ? p.ext_init_h + size_t(f) * 2 * N * N : nullptr,

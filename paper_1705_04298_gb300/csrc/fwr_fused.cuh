@@ -75,6 +75,13 @@ struct Layout {
     __host__ __device__ static size_t bytes_wf(int n) { return wf(n) + size_t(H + 1) * N * sizeof(T); }
 };
 
+// Prefetch [p, p + bytes) into L2, one 128-byte line per thread and step.
+__device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes) {
+    const char* b = static_cast<const char*>(p);
+    for (size_t o = size_t(threadIdx.x) * 128; o < bytes; o += size_t(blockDim.x) * 128)
+        asm volatile("prefetch.global.L2 [%0];\n" ::"l"(b + o));
+}
+
 __device__ __forceinline__ void store4(float* d, float a, float b, float c, float e) {
     *reinterpret_cast<float4*>(d) = make_float4(a, b, c, e);
 }
@@ -349,7 +356,7 @@ template <typename T, int N>
 __device__ __forceinline__ bool fused_frame(const FusedCtx<T, N>& c, const T* sl, const T* ext,
                                             const uint16_t* exth, T* phase, T* ext_out, int iters) {
     typedef typename cvec<T>::type V;
-    constexpr int R = N / 4, NT = 4 * N, H = N / 2, S = Layout<T, N>::S;
+    constexpr int R = N / 4, NT = 4 * N, S = Layout<T, N>::S;
     const int tid = threadIdx.x;
     V* const Z = c.Z;
     T* const xpart = c.xpart;
@@ -396,10 +403,14 @@ __device__ __forceinline__ bool fused_frame(const FusedCtx<T, N>& c, const T* sl
             store4(zp + 4, ex[2], ey[2], ex[3], ey[3]);
         }
     }
+    // measured slopes of the pupil cells into s0: the mask and slope loads do
+    // not depend on each other, so unrolled iterations keep them all in flight
+#pragma unroll 4
     for (int c = tid; c < nn; c += NT) {
-        if (mask[c]) {
+        const uint8_t m = __ldg(mask + c);
+        const T vx = sl[c], vy = sl[nn + c];
+        if (m) {
             const int i = c / n, j = c - i * n;
-            const T vx = sl[c], vy = sl[nn + c];
             finite &= isfinite(vx) && isfinite(vy);
             s0[i * ns + j] = mk(vx, vy);
         }
