@@ -285,7 +285,9 @@ __device__ __forceinline__ void fused_setup(FusedCtx<T, N>& c, unsigned char* sm
     }
     for (int i = tid; i < 4 * N; i += NT) pt[i] = tab.pt[i];
     // 1/|G|^2 weights in storage-column order (entry [ky][col] holds kx(col)),
-    // so the lanes of a warp read consecutive words
+    // so the lanes of a warp read consecutive words (unrolled: independent
+    // loads in flight together)
+#pragma unroll 8
     for (int i = tid; i < (H + 1) * N; i += NT) {
         const int col = i % N, src = (i / N) * N + (col >> 2) + R * (col & 3);
         iota[i] = tab.iota[src];

@@ -167,6 +167,7 @@ __device__ __forceinline__ void slab_setup(SlabCtx& c, unsigned char* smem, cons
         c.Tt[i] = tab.Tt[i];
     }
     for (int i = tid; i < 4 * SN; i += SNT) c.pt[i] = tab.pt[i];
+#pragma unroll 8
     for (int i = tid; i < c.nn; i += SNT) c.mask[i] = mask_g[i];
     __syncthreads();
 }
