@@ -50,6 +50,12 @@ __device__ __forceinline__ void cp_async4(void* dst, const void* src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+// prefetch [p, p + bytes) into L2, one 128-byte line per thread and step
+__device__ __forceinline__ void prefetch_lines_l2(const void* p, size_t bytes) {
+    const char* b = static_cast<const char*>(p);
+    for (size_t o = size_t(threadIdx.x) * 128; o < bytes; o += size_t(blockDim.x) * 128)
+        asm volatile("prefetch.global.L2 [%0];\n" ::"l"(b + o));
+}
 
 // Pass A over the 64 lines: 16-point DFT over n1 of elements 16 n1 + n2,
 // then the twiddle w^(n2 k1) (conjugate for the inverse), in place.
@@ -299,6 +305,14 @@ __device__ __forceinline__ bool slab_frame(const SlabCtx& c, const Tables<float>
                                           (mode == PERIODIC_FINAL_ONLY && it + 1 == iters));
         for (int b = 0; b < 4; ++b) {
             const int m0 = SL * b;
+            {
+                // this slab's measured slopes into L2 while it is loaded and transformed
+                const int p0 = max(0, m0 - off), p1 = min(n, m0 + SL - off);
+                if (p1 > p0) {
+                    prefetch_lines_l2(sl + p0 * n, size_t(p1 - p0) * n * sizeof(float));
+                    prefetch_lines_l2(sl + nn + p0 * n, size_t(p1 - p0) * n * sizeof(float));
+                }
+            }
             if (it < 0) {
                 for (int l = lb; l < SL; l += 2) {
                     const int g = (m0 + l) * SN + cc;
@@ -331,7 +345,7 @@ __device__ __forceinline__ bool slab_frame(const SlabCtx& c, const Tables<float>
             const int i0 = max(0, m0 - off), i1 = min(n, m0 + SL - off);
             const int j = tid & ((1 << c.pw) - 1);
             if (j < n) {
-#pragma unroll 4
+#pragma unroll 16
                 for (int i = i0 + (tid >> c.pw); i < i1; i += SNT >> c.pw) {
                     const float vx = __ldg(sl + i * n + j), vy = __ldg(sl + nn + i * n + j);
                     if (mask[i * n + j]) {
