@@ -28,6 +28,14 @@ Conventions (the paper leaves them open; each reading is listed in the design doc):
       Gy(u, v) = sinc(u) * exp(i pi u) * (exp(2i pi v) - 1)
   with the transverse factor set to 0 on the Nyquist row/column (the average
   of its two aliases), so that G is Hermitian on the grid.
+* Measurement-model variants (options of the same model):
+  - G_FRIED: the phase known at the lenslet corners, each slope the mean of
+    the lenslet's two edge differences: transverse factor cos(pi v) exp(i pi v);
+  - pixel = d_px / d > 0: the difference of Sec. 2 taken over d - d_px (the
+    correction to Eq. 4 for a pixelated detector), between the transverse
+    averages at the lenslet centre +- (d - d_px)/2 and scaled back to a slope
+    per lenslet: exp(2i pi u) - 1 becomes
+    2i sin(pi u (1 - pixel)) / (1 - pixel) exp(i pi u).
 * 1/|G|^2 is set to 0 where |G|^2 < 1e-14 (piston and the (-1/2, -1/2)
   waffle bin), so every reconstructed phase has zero mean over the grid.
 * The Wiener noise-to-signal ratio of Eq. 3 (gamma = 1) is
@@ -51,6 +59,10 @@ FILTER_LSQ = 0
 FILTER_WIENER = 1
 
 NULL_THRESHOLD = 1e-14
+
+# measurement models (transverse factor of G)
+G_AVERAGED = 0   # lenslet-averaged gradient (Eq. 4): sinc
+G_FRIED = 1      # corner samples, mean of the two edge differences: cos
 
 
 def next_pow2(x):
@@ -117,28 +129,40 @@ def signed_freq(N):
     return np.where(k < N // 2, k, k - N) / N
 
 
-def shift_factor(N):
+def shift_factor(N, pixel=0.0):
     """a(u) = exp(2i pi u) - 1: the difference across one pitch of a mode at
-    frequency u (gradient x lenslet sampling in Eq. 4)."""
+    frequency u (gradient x lenslet sampling in Eq. 4).  With pixel = d_px/d
+    > 0 the difference spans d - d_px about the lenslet centre and is scaled
+    by d / (d - d_px): 2i sin(pi u (1 - pixel)) / (1 - pixel) exp(i pi u)."""
     u = signed_freq(N)
-    return np.exp(2j * math.pi * u) - 1.0
+    if pixel == 0.0:
+        return np.exp(2j * math.pi * u) - 1.0
+    L = 1.0 - pixel
+    return 2j * np.sin(math.pi * u * L) / L * np.exp(1j * math.pi * u)
 
 
-def average_factor(N):
+def average_factor(N, g_model=G_AVERAGED):
     """T(u) = sinc(u) exp(i pi u): the average of a mode over one pitch in the
     transverse direction (the box Pi of Eq. 4).  On the Nyquist bin u = -1/2
-    the two aliases give -2i/pi and +2i/pi; their average, 0, is used."""
+    the two aliases give -2i/pi and +2i/pi; their average, 0, is used.
+    G_FRIED: the mean of the two corner samples, cos(pi u) exp(i pi u), which
+    is 0 on the Nyquist bin."""
     u = signed_freq(N)
-    T = np.sinc(u) * np.exp(1j * math.pi * u)
+    if g_model == G_FRIED:
+        T = np.cos(math.pi * u) * np.exp(1j * math.pi * u)
+    elif g_model == G_AVERAGED:
+        T = np.sinc(u) * np.exp(1j * math.pi * u)
+    else:
+        raise ValueError("unknown measurement model")
     T[N // 2] = 0.0
     return T
 
 
-def measurement_filters(N):
+def measurement_filters(N, g_model=G_AVERAGED, pixel=0.0):
     """Gx[ky, kx] and Gy[ky, kx]: the discrete Shack-Hartmann model (Eq. 4)
     in the Fourier domain, s~ = G~ phi~ (Eq. 1)."""
-    a = shift_factor(N)
-    T = average_factor(N)
+    a = shift_factor(N, pixel)
+    T = average_factor(N, g_model)
     Gx = np.outer(T, a)   # row factor depends on v (ky), column factor on u (kx)
     Gy = np.outer(a, T)
     return Gx, Gy
@@ -160,10 +184,11 @@ def von_karman_psd(N, r0_pitch, L0_pitch):
     return 0.023 * r0_pitch ** (-5.0 / 3.0) * (kappa2 + L0_pitch ** -2.0) ** (-11.0 / 6.0)
 
 
-def reconstruction_filters(N, filt, noise_var=0.0, r0_pitch=1.0, L0_pitch=1.0):
+def reconstruction_filters(N, filt, noise_var=0.0, r0_pitch=1.0, L0_pitch=1.0, g_model=G_AVERAGED,
+                           pixel=0.0):
     """Rx, Ry of Eq. 2.  LSQ: G*/|G|^2.  Wiener (Eq. 3, gamma = 1):
     G* / (|G|^2 + noise_var / W_phi).  Both are 0 at the nulls of |G|^2."""
-    Gx, Gy = measurement_filters(N)
+    Gx, Gy = measurement_filters(N, g_model, pixel)
     g2 = np.abs(Gx) ** 2 + np.abs(Gy) ** 2
     if filt == FILTER_LSQ:
         w = lsq_weight(Gx, Gy)
@@ -228,7 +253,7 @@ def gerchberg_iteration(sx, sy, s0x, s0y, P, Gx, Gy, iota):
 
 
 def gerchberg_extend(s0x, s0y, P, iters, periodic=PERIODIC_BEFORE_EACH_FFT,
-                     ext_init=None, history=None):
+                     ext_init=None, history=None, g_model=G_AVERAGED, pixel=0.0):
     """Run `iters` Gerchberg iterations from the embedded slopes (Algorithm 1).
 
     ext_init: optional (2, N, N) initial extension used outside the pupil.
@@ -237,7 +262,7 @@ def gerchberg_extend(s0x, s0y, P, iters, periodic=PERIODIC_BEFORE_EACH_FFT,
     periodic condition where the mode asks for it (Algorithm 1 step 5).
     """
     N = s0x.shape[0]
-    Gx, Gy = measurement_filters(N)
+    Gx, Gy = measurement_filters(N, g_model, pixel)
     iota = lsq_weight(Gx, Gy)
     if ext_init is None:
         sx, sy = s0x.copy(), s0y.copy()
@@ -263,10 +288,11 @@ def final_reconstruct(sx, sy, Rx, Ry):
 
 def reconstruct(slopes, mask, pad_factor, iters, filt=FILTER_LSQ, noise_var=0.0,
                 r0_pitch=1.0, L0_pitch=1.0, periodic=PERIODIC_BEFORE_EACH_FFT,
-                ext_init=None, history=None):
+                ext_init=None, history=None, g_model=G_AVERAGED, pixel=0.0):
     """Whole path for one frame: embed -> Gerchberg extension -> final filter.
 
     slopes: (2, n, n) x then y slopes in radians per lenslet; mask: (n, n).
+    g_model, pixel: the measurement model (G_AVERAGED or G_FRIED; d_px / d).
     Returns (phase N x N, extended slopes (2, N, N)).
     """
     slopes = np.asarray(slopes, dtype=np.float64)
@@ -274,8 +300,8 @@ def reconstruct(slopes, mask, pad_factor, iters, filt=FILTER_LSQ, noise_var=0.0,
     n = mask.shape[0]
     N = grid_size(n, pad_factor)
     s0x, s0y, P = embed(slopes, mask, N)
-    sx, sy = gerchberg_extend(s0x, s0y, P, iters, periodic, ext_init, history)
-    Rx, Ry = reconstruction_filters(N, filt, noise_var, r0_pitch, L0_pitch)
+    sx, sy = gerchberg_extend(s0x, s0y, P, iters, periodic, ext_init, history, g_model, pixel)
+    Rx, Ry = reconstruction_filters(N, filt, noise_var, r0_pitch, L0_pitch, g_model, pixel)
     phase = final_reconstruct(sx, sy, Rx, Ry)
     return phase, np.stack([sx, sy])
 
