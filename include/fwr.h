@@ -95,6 +95,26 @@ typedef enum {
 #define FWR_PERIODIC_BEFORE_EACH_FFT 0 /* before every forward FFT, the final one included (default) */
 #define FWR_PERIODIC_FINAL_ONLY 1      /* once, before the final reconstruction (Algorithm 1 step 5) */
 #define FWR_PERIODIC_NONE 2            /* never */
+/*
+ * Measurement model G of Eq. 4 (Sec. 2); both keys rebuild the plan's filter
+ * tables in FP64 (the device is synchronised first, since running launches
+ * may read the old tables). Batches and warm starts made from the plan keep
+ * the tables they were made with.
+ *   FWR_OPT_G_MODEL: the transverse factor of G, i.e. how a slope averages
+ *     across the lenslet. FWR_G_AVERAGED (default): the lenslet-averaged
+ *     gradient, Gx = a(u) sinc(v) e^{i pi v}. FWR_G_FRIED: phase known at the
+ *     lenslet corners, each slope the mean of the two edge differences,
+ *     Gx = a(u) cos(pi v) e^{i pi v}. (Gy: u and v exchanged.)
+ *   FWR_OPT_PIXEL: d_px / d in [0, 0.5], the detector pixel over the lenslet
+ *     pitch. The slope is the difference of the transverse averages over
+ *     d - d_px (the pixel correction of Sec. 2), per lenslet:
+ *     a(u) = 2i sin(pi u (1 - d_px/d)) / (1 - d_px/d) e^{i pi u}; 0 (default)
+ *     gives a(u) = e^{2 i pi u} - 1. Six pixels per lenslet: 1/6.
+ */
+#define FWR_OPT_G_MODEL 3
+#define FWR_OPT_PIXEL 4
+#define FWR_G_AVERAGED 0
+#define FWR_G_FRIED 1
 
 /*
  * Create a plan for an n x n lenslet array (Sec. 2; Algorithm 1 input).

@@ -68,7 +68,7 @@ struct HostTables {
     std::vector<double> iota, wfin; // (N/2+1) * N
 };
 
-HostTables build_tables(int N, int filter, double noise_var, double r0, double L0) {
+HostTables build_tables(int N, int filter, double noise_var, double r0, double L0, int g_model, double pixel) {
     HostTables h;
     h.tw.resize(2 * N);
     h.A.resize(2 * N);
@@ -78,15 +78,28 @@ HostTables build_tables(int N, int filter, double noise_var, double r0, double L
         h.tw[2 * j] = std::cos(ang);
         h.tw[2 * j + 1] = -std::sin(ang);
         const double u = signed_freq(j, N);
-        // a(u) = e^{2 i pi u} - 1; exact at u = 0 and u = -1/2
-        double ar = std::cos(2.0 * kPi * u) - 1.0, ai = std::sin(2.0 * kPi * u);
+        // a(u) = e^{2 i pi u} - 1; exact at u = 0 and u = -1/2. With the pixel
+        // correction the difference spans d - d_px about the lenslet centre,
+        // per lenslet: 2i sin(pi u L) / L e^{i pi u}, L = 1 - d_px / d (real on
+        // the Nyquist bin, as G must be there)
+        double ar, ai;
+        if (pixel == 0.0) {
+            ar = std::cos(2.0 * kPi * u) - 1.0;
+            ai = std::sin(2.0 * kPi * u);
+            if (j == N / 2) { ar = -2.0; ai = 0.0; }
+        } else {
+            const double L = 1.0 - pixel, sl = std::sin(kPi * u * L) / L;
+            ar = -2.0 * sl * std::sin(kPi * u);
+            ai = 2.0 * sl * std::cos(kPi * u);
+            if (j == N / 2) ai = 0.0;
+        }
         if (j == 0) ar = ai = 0.0;
-        if (j == N / 2) { ar = -2.0; ai = 0.0; }
         h.A[2 * j] = ar;
         h.A[2 * j + 1] = ai;
-        // T(u) = sinc(u) e^{i pi u}; the Nyquist bin takes the mean of its two
-        // aliases, which is 0
-        const double s = sinc(u);
+        // T(u) = sinc(u) e^{i pi u} (lenslet average) or cos(pi u) e^{i pi u}
+        // (mean of two corner samples); the Nyquist bin takes the mean of its
+        // two aliases, which is 0
+        const double s = g_model == FWR_G_FRIED ? std::cos(kPi * u) : sinc(u);
         h.Tt[2 * j] = (j == N / 2) ? 0.0 : s * std::cos(kPi * u);
         h.Tt[2 * j + 1] = (j == N / 2) ? 0.0 : s * std::sin(kPi * u);
     }
@@ -223,7 +236,7 @@ fwr_status fwr_plan_create(fwr_plan** out, int n, double pad_factor, const uint8
         st = cuda_fail(e, "plan allocation");
     }
     if (st == FWR_OK) {
-        HostTables h = build_tables(N, filter, noise_var, r0, L0);
+        HostTables h = build_tables(N, filter, noise_var, r0, L0, p->g_model, p->pixel);
         st = upload_tables<float>(h, N, p->f32);
         if (st == FWR_OK && N <= 64) st = upload_tables<double>(h, N, p->f64);
     }
@@ -269,8 +282,40 @@ int fwr_plan_grid(const fwr_plan* p) { return p ? p->N : -1; }
 
 int fwr_plan_valid_count(const fwr_plan* p) { return p ? p->nvalid : -1; }
 
+// The plan's filter tables again, for its current measurement model; the
+// device is synchronised first (running launches may read the old tables).
+static fwr_status rebuild_tables(fwr_plan* p) {
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(p->device);
+    cudaError_t e = cudaDeviceSynchronize();
+    fwr_status st = e == cudaSuccess ? FWR_OK : cuda_fail(e, "synchronise before the table rebuild");
+    if (st == FWR_OK) {
+        free_tables(p->f32);
+        free_tables(p->f64);
+        HostTables h = build_tables(p->N, p->filter, p->noise_var, p->r0, p->L0, p->g_model, p->pixel);
+        st = upload_tables<float>(h, p->N, p->f32);
+        if (st == FWR_OK && p->N <= 64) st = upload_tables<double>(h, p->N, p->f64);
+    }
+    cudaSetDevice(prev);
+    return st;
+}
+
 fwr_status fwr_plan_set_option(fwr_plan* p, int key, double value) {
     if (!p) return FWR_ERR_ARG;
+    if (key == FWR_OPT_G_MODEL) {
+        const int v = int(value);
+        if (double(v) != value || (v != FWR_G_AVERAGED && v != FWR_G_FRIED)) return FWR_ERR_ARG;
+        if (v == p->g_model) return FWR_OK;
+        p->g_model = v;
+        return rebuild_tables(p);
+    }
+    if (key == FWR_OPT_PIXEL) {
+        if (!(value >= 0.0 && value <= 0.5)) return FWR_ERR_ARG;
+        if (value == p->pixel) return FWR_OK;
+        p->pixel = value;
+        return rebuild_tables(p);
+    }
     if (key == FWR_OPT_TRANSFORM) {
         const int v = int(value);
         if (double(v) != value || (v != FWR_TRANSFORM_FFT && v != FWR_TRANSFORM_DFT_BF16X3)) return FWR_ERR_ARG;

@@ -44,6 +44,8 @@ cudaError_t launch_warm_bf16(fwr_plan* p, const float* slopes, const uint16_t* e
 struct fwr_plan {
     int n = 0, N = 0, off = 0, filter = 0, periodic = FWR_PERIODIC_BEFORE_EACH_FFT, nvalid = 0;
     int transform = FWR_TRANSFORM_FFT;
+    int g_model = FWR_G_AVERAGED;   // measurement model of the filter tables
+    double pixel = 0.0;             // d_px / d of the filter tables
     int device = 0;
     double noise_var = 0, r0 = 0, L0 = 0;
     uint8_t* d_mask = nullptr;

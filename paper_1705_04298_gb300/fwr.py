@@ -22,6 +22,10 @@ PERIODIC_FINAL_ONLY = 1
 PERIODIC_NONE = 2
 OPT_PERIODIC = 1
 OPT_TRANSFORM = 2
+OPT_G_MODEL = 3
+OPT_PIXEL = 4
+G_AVERAGED = 0
+G_FRIED = 1
 TRANSFORM_FFT = 0
 TRANSFORM_DFT_BF16X3 = 1
 STATIC_SCRATCH_GRIDS = 16
@@ -161,6 +165,12 @@ class Plan:
     def set_periodic(self, mode):
         _check(self._lib.fwr_plan_set_option(self._h, OPT_PERIODIC, float(mode)), "fwr_plan_set_option")
         self.periodic = mode
+
+    def set_model(self, g_model=G_AVERAGED, pixel=0.0):
+        """Measurement model of the filter tables: G_AVERAGED or G_FRIED and
+        d_px / d in [0, 0.5]; rebuilds the tables (synchronises the device)."""
+        _check(self._lib.fwr_plan_set_option(self._h, OPT_G_MODEL, float(g_model)), "fwr_plan_set_option")
+        _check(self._lib.fwr_plan_set_option(self._h, OPT_PIXEL, float(pixel)), "fwr_plan_set_option")
 
     def set_transform(self, mode):
         """TRANSFORM_FFT (default) or TRANSFORM_DFT_BF16X3 (tensor-core split-BF16

@@ -325,3 +325,56 @@ def test_misaligned_phase_and_warm_start_are_refused(fwr):
         plan.reconstruct(s, 2, ext_init=ext[1:].view(1, 2, N, N))
     ok = plan.reconstruct(s, 2, flat[:N * N].view(1, N, N))
     assert torch.isfinite(ok).all()
+
+
+# ------------------------------------------ measurement-model variants ----
+
+MODELS = [(1, 0.0), (0, 1.0 / 6.0), (1, 1.0 / 6.0)]
+
+
+@pytest.mark.parametrize("g_model,pixel", MODELS)
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_model_variants_small(fwr, g_model, pixel, precision):
+    """Fried geometry and the d - d_px pixel correction (FWR_OPT_G_MODEL,
+    FWR_OPT_PIXEL) against the oracle with the same model: 30x30 lenslets on
+    64^2, Wiener, every periodic mode."""
+    n, pad, k, sigma = 30, 2.0, 4, 0.1
+    r0p, L0p = synth.pitch_units(n, 0.15, 25.0)
+    sl, _, mask = synth.batch(n, 2, 91, sigma)
+    dtype = torch.float64 if precision == "fp64" else torch.float32
+    tol = FP64_TOL if precision == "fp64" else FP32_TOL
+    for periodic in (0, 1, 2):
+        plan = make_plan(fwr, mask, pad, fwr.WIENER, sigma ** 2, r0p, L0p, periodic)
+        plan.set_model(g_model, pixel)
+        s = torch.tensor(sl, dtype=dtype, device="cuda")
+        ph = (plan.reconstruct_f64 if precision == "fp64" else plan.reconstruct)(s, k).cpu().numpy()
+        for f in range(2):
+            ref, _ = oracle.reconstruct(sl[f], mask, pad, k, oracle.FILTER_WIENER, sigma ** 2, r0p, L0p,
+                                        periodic, g_model=g_model, pixel=pixel)
+            assert rel_rms(ph[f], ref) <= tol, (periodic, f, rel_rms(ph[f], ref))
+
+
+@pytest.mark.parametrize("n,pad,k", [(40, 3.2, 5), (80, 3.2, 2)])
+def test_model_variants_large_grids(fwr, n, pad, k):
+    """The same on 128^2 (fused kernel) and 256^2 (slab kernel), Fried with
+    six pixels per lenslet; setting the default model back reproduces the
+    default path bit for bit."""
+    sigma = 0.05
+    r0p, L0p = synth.pitch_units(n, 0.15, 25.0)
+    sl, _, mask = synth.batch(n, 3, 17, sigma)
+    plan = make_plan(fwr, mask, pad, fwr.WIENER, sigma ** 2, r0p, L0p)
+    s = torch.tensor(sl, dtype=torch.float32, device="cuda")
+    base = plan.reconstruct(s, k).cpu()
+    plan.set_model(fwr.G_FRIED, 1.0 / 6.0)
+    ph = plan.reconstruct(s, k).cpu().numpy()
+    for f in range(3):
+        ref, _ = oracle.reconstruct(sl[f], mask, pad, k, oracle.FILTER_WIENER, sigma ** 2, r0p, L0p,
+                                    g_model=oracle.G_FRIED, pixel=1.0 / 6.0)
+        assert rel_rms(ph[f], ref) <= FP32_TOL, (f, rel_rms(ph[f], ref))
+    assert not torch.equal(torch.tensor(ph), base)
+    plan.set_model(fwr.G_AVERAGED, 0.0)
+    assert torch.equal(plan.reconstruct(s, k).cpu(), base)
+    with pytest.raises(fwr.FwrError):
+        plan.set_model(2, 0.0)
+    with pytest.raises(fwr.FwrError):
+        plan.set_model(fwr.G_AVERAGED, 0.6)
