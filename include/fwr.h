@@ -115,6 +115,25 @@ typedef enum {
 #define FWR_OPT_PIXEL 4
 #define FWR_G_AVERAGED 0
 #define FWR_G_FRIED 1
+/*
+ * FWR_OPT_EXTENSION: the slopes outside the pupil before the first iteration
+ * when no warm start is passed. FWR_EXT_ZERO (default): zero. FWR_EXT_HUDGIN:
+ * the Hudgin extension of Sec. 3.1 (after Poyneer et al.): every x slope
+ * outside the pupil takes the measured x slope at the top or bottom pupil
+ * edge of its column (up or down to the grid edge), every y slope the
+ * measured y slope at the left or right pupil edge of its row; gaps inside a
+ * column or row and columns or rows without pupil cells stay 0. With 0
+ * iterations and the periodic condition this is the paper's Hudgin method;
+ * with more, a Gerchberg loop started from it. Computed inside the kernels
+ * from the staged slopes (no extra memory traffic). Supported by the FFT
+ * paths of fwr_reconstruct_ex / fwr_reconstruct_f64 / fwr_reconstruct_host /
+ * fwr_reconstruct_static; the DFT-as-GEMM transform and the generic kernel
+ * for large pupils on 128x128 grids return FWR_ERR_UNSUPPORTED; batches and
+ * warm-start objects start from their own extension.
+ */
+#define FWR_OPT_EXTENSION 5
+#define FWR_EXT_ZERO 0
+#define FWR_EXT_HUDGIN 1
 
 /*
  * Create a plan for an n x n lenslet array (Sec. 2; Algorithm 1 input).

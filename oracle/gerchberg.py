@@ -234,6 +234,37 @@ def embed(slopes, mask, N):
     return sx, sy, P
 
 
+def hudgin_extension(s0x, s0y, P):
+    """The Hudgin extension of Sec. 3.1 (from Poyneer et al.): outside the
+    pupil, every x slope takes the measured x slope at the top or bottom edge
+    of the pupil in its column (the nearer end, going up or down to the grid
+    edge), and every y slope the measured y slope at the left or right edge of
+    the pupil in its row. Gaps between two pupil cells of a column (row) and
+    columns (rows) without pupil cells stay 0. Returns (2, N, N)."""
+    N = s0x.shape[0]
+    ex = np.zeros((N, N))
+    ey = np.zeros((N, N))
+    for col in range(N):
+        rows = [m for m in range(N) if P[m, col]]
+        if rows:
+            top, bot = rows[0], rows[-1]
+            for m in range(N):
+                if m < top:
+                    ex[m, col] = s0x[top, col]
+                elif m > bot:
+                    ex[m, col] = s0x[bot, col]
+    for row in range(N):
+        cols = [n for n in range(N) if P[row, n]]
+        if cols:
+            left, right = cols[0], cols[-1]
+            for n in range(N):
+                if n < left:
+                    ey[row, n] = s0y[row, left]
+                elif n > right:
+                    ey[row, n] = s0y[row, right]
+    return np.stack([ex, ey])
+
+
 def gerchberg_iteration(sx, sy, s0x, s0y, P, Gx, Gy, iota):
     """One pass of Algorithm 1, steps 1-4."""
     # step 1: Fourier transform of both slope fields
@@ -256,7 +287,8 @@ def gerchberg_extend(s0x, s0y, P, iters, periodic=PERIODIC_BEFORE_EACH_FFT,
                      ext_init=None, history=None, g_model=G_AVERAGED, pixel=0.0):
     """Run `iters` Gerchberg iterations from the embedded slopes (Algorithm 1).
 
-    ext_init: optional (2, N, N) initial extension used outside the pupil.
+    ext_init: optional (2, N, N) initial extension used outside the pupil, or
+    the string "hudgin" for the Hudgin extension of the measured slopes.
     history: optional list; receives (sx, sy) after every iteration.
     Returns the slopes that enter the final reconstruction, after the
     periodic condition where the mode asks for it (Algorithm 1 step 5).
@@ -264,6 +296,10 @@ def gerchberg_extend(s0x, s0y, P, iters, periodic=PERIODIC_BEFORE_EACH_FFT,
     N = s0x.shape[0]
     Gx, Gy = measurement_filters(N, g_model, pixel)
     iota = lsq_weight(Gx, Gy)
+    if isinstance(ext_init, str):
+        if ext_init != "hudgin":
+            raise ValueError("unknown extension")
+        ext_init = hudgin_extension(s0x, s0y, P)
     if ext_init is None:
         sx, sy = s0x.copy(), s0y.copy()
     else:

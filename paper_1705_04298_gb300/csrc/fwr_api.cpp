@@ -228,9 +228,23 @@ fwr_status fwr_plan_create(fwr_plan** out, int n, double pad_factor, const uint8
     std::vector<uint8_t> m(size_t(n) * n);
     for (int i = 0; i < n * n; ++i) m[i] = pupil_mask[i] ? 1 : 0;
     p->h_mask = m;
+    // pupil edges of every lenslet column (first, last row) and row (first,
+    // last column) for the Hudgin extension; -1 without pupil cells
+    std::vector<int16_t> hud(4 * size_t(n), int16_t(-1));
+    for (int i = 0; i < n; ++i) {
+        for (int j = 0; j < n; ++j) {
+            if (!m[size_t(i) * n + j]) continue;
+            if (hud[j] < 0) hud[j] = int16_t(i);
+            hud[n + j] = int16_t(i);
+            if (hud[2 * n + i] < 0) hud[2 * n + i] = int16_t(j);
+            hud[3 * n + i] = int16_t(j);
+        }
+    }
     fwr_status st = FWR_OK;
     if ((e = cudaMalloc(&p->d_mask, m.size())) != cudaSuccess ||
         (e = cudaMemcpy(p->d_mask, m.data(), m.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMalloc(&p->d_hud, hud.size() * sizeof(int16_t))) != cudaSuccess ||
+        (e = cudaMemcpy(p->d_hud, hud.data(), hud.size() * sizeof(int16_t), cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMalloc(&p->d_status, sizeof(unsigned))) != cudaSuccess ||
         (e = cudaMemset(p->d_status, 0, sizeof(unsigned))) != cudaSuccess) {
         st = cuda_fail(e, "plan allocation");
@@ -265,6 +279,7 @@ void fwr_plan_destroy(fwr_plan* p) {
     free_tables(p->f32);
     free_tables(p->f64);
     cudaFree(p->d_mask);
+    cudaFree(p->d_hud);
     cudaFree(p->d_status);
     cudaFree(p->d_scratch);
     cudaFree(p->d_dftws);
@@ -338,6 +353,12 @@ fwr_status fwr_plan_set_option(fwr_plan* p, int key, double value) {
         p->transform = v;
         return FWR_OK;
     }
+    if (key == FWR_OPT_EXTENSION) {
+        const int v = int(value);
+        if (double(v) != value || (v != FWR_EXT_ZERO && v != FWR_EXT_HUDGIN)) return FWR_ERR_ARG;
+        p->extension = v;
+        return FWR_OK;
+    }
     if (key == FWR_OPT_PERIODIC) {
         const int v = int(value);
         if (double(v) != value || v < FWR_PERIODIC_BEFORE_EACH_FFT || v > FWR_PERIODIC_NONE) return FWR_ERR_ARG;
@@ -379,6 +400,12 @@ fwr_status fwr_reconstruct_ex(fwr_plan* p, const float* slopes, const float* ext
     k.iters = iters;
     k.periodic = p->periodic;
     k.status = p->d_status;
+    const bool hudgin = p->extension == FWR_EXT_HUDGIN && !ext_init;
+    if (hudgin) {
+        if (p->transform == FWR_TRANSFORM_DFT_BF16X3 || (p->N != 256 && !fwr::fused_supported(p->N, 4, p->n)))
+            return FWR_ERR_UNSUPPORTED;
+        k.hud = p->d_hud;
+    }
     cudaError_t e;
     if (p->transform == FWR_TRANSFORM_DFT_BF16X3) {
         if (p->N >= 128) {
@@ -434,6 +461,7 @@ fwr_status fwr_reconstruct_static(fwr_plan* p, const float* slopes, int n_frames
     k.iters = iters;
     k.periodic = p->periodic;
     k.status = p->d_status;
+    if (p->extension == FWR_EXT_HUDGIN) k.hud = p->d_hud;
     cudaError_t e = fwr::launch_slab_static(k, ctas, static_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? FWR_OK : cuda_fail(e, "static-scratch launch");
 }
@@ -458,6 +486,10 @@ fwr_status fwr_reconstruct_f64(fwr_plan* p, const double* slopes, const double* 
     k.iters = iters;
     k.periodic = p->periodic;
     k.status = p->d_status;
+    if (p->extension == FWR_EXT_HUDGIN && !ext_init) {
+        if (!fwr::fused_supported(p->N, 8, p->n)) return FWR_ERR_UNSUPPORTED;
+        k.hud = p->d_hud;
+    }
     cudaError_t e = fwr::fused_supported(p->N, 8, p->n)
                         ? fwr::launch_fused_f64(p->N, k, static_cast<cudaStream_t>(stream))
                         : fwr::launch_basic_f64(p->N, k, static_cast<cudaStream_t>(stream));

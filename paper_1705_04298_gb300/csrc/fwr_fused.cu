@@ -28,7 +28,7 @@ fused_kernel(Params<T> p) {
                                     p.ext_init ? p.ext_init + size_t(f) * 2 * N * N : nullptr,
                                     p.ext_init_h ? p.ext_init_h + size_t(f) * 2 * N * N : nullptr,
                                     p.phase ? p.phase + size_t(f) * N * N : nullptr,
-                                    p.ext_out ? p.ext_out + size_t(f) * 2 * N * N : nullptr, p.iters);
+                                    p.ext_out ? p.ext_out + size_t(f) * 2 * N * N : nullptr, p.iters, p.hud);
         __syncthreads();
     }
     if (!finite) atomicOr(&s_bad, 1);

@@ -220,6 +220,26 @@ __device__ __forceinline__ void pass2(V* Z, const V* tw, const V* tw2) {
 
 }  // namespace
 
+// Hudgin extension value of grid cell (row, col) outside the pupil, lenslet
+// (i, j) = (row - off, col - off): the x slope of the nearer pupil edge of
+// its column when above or below the pupil span, the y slope of the nearer
+// pupil edge of its row when left or right of it, else 0 (see Params::hud).
+// s0 holds the measured slopes of the pupil cells (row stride ns).
+template <typename V>
+__device__ __forceinline__ V hudgin_cell(const V* s0, int ns, const int16_t* hud, int n, int i, int j) {
+    typedef decltype(V().x) T;
+    T hx = T(0), hy = T(0);
+    if (j >= 0 && j < n) {
+        const int t = __ldg(hud + j), b = __ldg(hud + n + j);
+        if (t >= 0 && (i < t || i > b)) hx = s0[(i < t ? t : b) * ns + j].x;
+    }
+    if (i >= 0 && i < n) {
+        const int l = __ldg(hud + 2 * n + i), rt = __ldg(hud + 3 * n + i);
+        if (l >= 0 && (j < l || j > rt)) hy = s0[i * ns + (j < l ? l : rt)].y;
+    }
+    return mk(hx, hy);
+}
+
 // Per-CTA state of the main kernel for one plan: shared-memory layout and
 // the per-thread roles and constants.
 template <typename T, int N>
@@ -356,7 +376,8 @@ __device__ __forceinline__ void fused_setup(FusedCtx<T, N>& c, unsigned char* sm
 // threads that saw a non-finite measured slope.
 template <typename T, int N>
 __device__ __forceinline__ bool fused_frame(const FusedCtx<T, N>& c, const T* sl, const T* ext,
-                                            const uint16_t* exth, T* phase, T* ext_out, int iters) {
+                                            const uint16_t* exth, T* phase, T* ext_out, int iters,
+                                            const int16_t* hud = nullptr) {
     typedef typename cvec<T>::type V;
     constexpr int R = N / 4, NT = 4 * N, S = Layout<T, N>::S;
     const int tid = threadIdx.x;
@@ -419,7 +440,7 @@ __device__ __forceinline__ bool fused_frame(const FusedCtx<T, N>& c, const T* sl
     }
     __syncthreads();
 
-    // embed: measurement in the pupil, warm start (or zero) outside
+    // embed: measurement in the pupil, warm start, Hudgin extension or zero outside
     V x[R];
 #pragma unroll
     for (int n1 = 0; n1 < R; ++n1) {
@@ -427,6 +448,8 @@ __device__ __forceinline__ bool fused_frame(const FusedCtx<T, N>& c, const T* sl
             x[n1] = s0row[4 * n1];
         } else if (warm) {
             x[n1] = rowp[4 * n1];
+        } else if (hud) {
+            x[n1] = hudgin_cell(s0, ns, hud, n, r - c.off, 4 * n1 + n2 - c.off);
         } else {
             x[n1] = mk(T(0), T(0));
         }

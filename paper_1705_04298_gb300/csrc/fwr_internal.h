@@ -34,6 +34,11 @@ template <typename T> struct Params {
     int n = 0, off = 0, F = 0, iters = 0, periodic = 0;
     unsigned* status = nullptr;          // sticky device status bits
     int wf_smem = 0;                     // fused kernel: final weights resident in shared memory (set by its launcher)
+    // Hudgin extension as the initial extension (no warm start given): per
+    // lenslet column j the first / last pupil row, hud[j] / hud[n + j], per
+    // row i the first / last pupil column, hud[2n + i] / hud[3n + i]; -1 where
+    // the column or row has no pupil cell. nullptr: zero extension.
+    const int16_t* hud = nullptr;
 };
 
 // Where Eq. PC is applied (same values as FWR_PERIODIC_* in fwr.h).

@@ -45,6 +45,8 @@ struct fwr_plan {
     int n = 0, N = 0, off = 0, filter = 0, periodic = FWR_PERIODIC_BEFORE_EACH_FFT, nvalid = 0;
     int transform = FWR_TRANSFORM_FFT;
     int g_model = FWR_G_AVERAGED;   // measurement model of the filter tables
+    int extension = FWR_EXT_ZERO;   // initial extension without a warm start
+    int16_t* d_hud = nullptr;       // [4][n]: pupil edges per column and row (Hudgin extension)
     double pixel = 0.0;             // d_px / d of the filter tables
     int device = 0;
     double noise_var = 0, r0 = 0, L0 = 0;

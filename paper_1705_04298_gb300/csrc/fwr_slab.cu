@@ -26,7 +26,7 @@ slab_kernel(Params<float> p, float2* scratch) {
     for (int f = blockIdx.x; f < p.F; f += gridDim.x) {
         finite &= slab_frame(c, p.tab, p.slopes + size_t(f) * 2 * nn,
                              p.ext_init ? p.ext_init + size_t(f) * 2 * SN * SN : nullptr,
-                             p.phase + size_t(f) * SN * SN, p.iters, G);
+                             p.phase + size_t(f) * SN * SN, p.iters, G, p.hud);
         __syncthreads();
     }
     if (!finite) atomicOr(&s_bad, 1);

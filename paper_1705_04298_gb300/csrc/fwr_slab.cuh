@@ -190,7 +190,8 @@ __device__ __forceinline__ void slab_setup(SlabCtx& c, unsigned char* smem, cons
 // and takes the lines j = tid / 256 + 2 i, so the ky factors stay in registers
 // and the kx factors are warp-uniform.
 __device__ __forceinline__ bool slab_frame(const SlabCtx& c, const Tables<float>& tab, const float* sl,
-                                           const float* ext, float* phase, int iters, float2* G) {
+                                           const float* ext, float* phase, int iters, float2* G,
+                                           const int16_t* hud = nullptr) {
     const int tid = threadIdx.x;
     float2* const Lb = c.Lb;
     const float2* const tw = c.tw;
@@ -316,7 +317,23 @@ __device__ __forceinline__ bool slab_frame(const SlabCtx& c, const Tables<float>
             if (it < 0) {
                 for (int l = lb; l < SL; l += 2) {
                     const int g = (m0 + l) * SN + cc;
-                    Lb[l * SLS + cc] = ext ? make_float2(ext[g], ext[SN * SN + g]) : make_float2(0.f, 0.f);
+                    float2 v = make_float2(0.f, 0.f);
+                    if (ext) {
+                        v = make_float2(ext[g], ext[SN * SN + g]);
+                    } else if (hud) {
+                        // Hudgin extension from the measured slopes of the pupil
+                        // edges (the pupil cells are overwritten below)
+                        const int i = m0 + l - off, j = cc - off;
+                        if (j >= 0 && j < n) {
+                            const int t = __ldg(hud + j), b2 = __ldg(hud + n + j);
+                            if (t >= 0 && (i < t || i > b2)) v.x = __ldg(sl + (i < t ? t : b2) * n + j);
+                        }
+                        if (i >= 0 && i < n) {
+                            const int le = __ldg(hud + 2 * n + i), rt = __ldg(hud + 3 * n + i);
+                            if (le >= 0 && (j < le || j > rt)) v.y = __ldg(sl + nn + i * n + (j < le ? le : rt));
+                        }
+                    }
+                    Lb[l * SLS + cc] = v;
                 }
             } else {
                 {

@@ -26,6 +26,9 @@ OPT_G_MODEL = 3
 OPT_PIXEL = 4
 G_AVERAGED = 0
 G_FRIED = 1
+OPT_EXTENSION = 5
+EXT_ZERO = 0
+EXT_HUDGIN = 1
 TRANSFORM_FFT = 0
 TRANSFORM_DFT_BF16X3 = 1
 STATIC_SCRATCH_GRIDS = 16
@@ -171,6 +174,11 @@ class Plan:
         d_px / d in [0, 0.5]; rebuilds the tables (synchronises the device)."""
         _check(self._lib.fwr_plan_set_option(self._h, OPT_G_MODEL, float(g_model)), "fwr_plan_set_option")
         _check(self._lib.fwr_plan_set_option(self._h, OPT_PIXEL, float(pixel)), "fwr_plan_set_option")
+
+    def set_extension(self, mode):
+        """EXT_ZERO (default) or EXT_HUDGIN: the slopes outside the pupil
+        before the first iteration when no warm start is given."""
+        _check(self._lib.fwr_plan_set_option(self._h, OPT_EXTENSION, float(mode)), "fwr_plan_set_option")
 
     def set_transform(self, mode):
         """TRANSFORM_FFT (default) or TRANSFORM_DFT_BF16X3 (tensor-core split-BF16

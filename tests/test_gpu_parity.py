@@ -378,3 +378,65 @@ def test_model_variants_large_grids(fwr, n, pad, k):
         plan.set_model(2, 0.0)
     with pytest.raises(fwr.FwrError):
         plan.set_model(fwr.G_AVERAGED, 0.6)
+
+
+# ------------------------------------------------- Hudgin extension -------
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("k,periodic", [(0, 0), (3, 0), (2, 2)])
+def test_hudgin_extension_small(fwr, precision, k, periodic):
+    """FWR_OPT_EXTENSION = FWR_EXT_HUDGIN against the oracle's Hudgin start:
+    30x30 lenslets on 64^2, LSQ. k = 0 with the periodic condition is the
+    paper's Hudgin method."""
+    n, pad, sigma = 30, 2.0, 0.05
+    sl, _, mask = synth.batch(n, 2, 123, sigma)
+    plan = make_plan(fwr, mask, pad, fwr.LSQ, 0.0, 1.0, 1.0, periodic)
+    plan.set_extension(fwr.EXT_HUDGIN)
+    dtype = torch.float64 if precision == "fp64" else torch.float32
+    tol = FP64_TOL if precision == "fp64" else FP32_TOL
+    s = torch.tensor(sl, dtype=dtype, device="cuda")
+    ph = (plan.reconstruct_f64 if precision == "fp64" else plan.reconstruct)(s, k).cpu().numpy()
+    for f in range(2):
+        ref, _ = oracle.reconstruct(sl[f], mask, pad, k, oracle.FILTER_LSQ, periodic=periodic, ext_init="hudgin")
+        assert rel_rms(ph[f], ref) <= tol, (f, rel_rms(ph[f], ref))
+
+
+@pytest.mark.parametrize("n,pad,k", [(40, 3.2, 0), (40, 3.2, 2), (80, 3.2, 0), (80, 3.2, 1)])
+def test_hudgin_extension_large_grids(fwr, n, pad, k):
+    """The same on 128^2 (fused kernel) and 256^2 (slab kernel), Wiener; the
+    host path and an explicit warm start (which takes precedence) behave as
+    with the zero extension."""
+    sigma = 0.05
+    r0p, L0p = synth.pitch_units(n, 0.15, 25.0)
+    sl, _, mask = synth.batch(n, 3, 29, sigma)
+    plan = make_plan(fwr, mask, pad, fwr.WIENER, sigma ** 2, r0p, L0p)
+    s = torch.tensor(sl, dtype=torch.float32, device="cuda")
+    zero = plan.reconstruct(s, k).cpu()
+    plan.set_extension(fwr.EXT_HUDGIN)
+    ph = plan.reconstruct(s, k).cpu()
+    for f in range(3):
+        ref, _ = oracle.reconstruct(sl[f], mask, pad, k, oracle.FILTER_WIENER, sigma ** 2, r0p, L0p,
+                                    ext_init="hudgin")
+        assert rel_rms(ph[f].numpy(), ref) <= FP32_TOL, (f, rel_rms(ph[f].numpy(), ref))
+    assert not torch.equal(ph, zero)
+    sh = torch.tensor(sl, dtype=torch.float32).pin_memory()
+    out = torch.empty((3, plan.N, plan.N), dtype=torch.float32).pin_memory()
+    plan.reconstruct_host(sh, k, out)
+    torch.cuda.synchronize()
+    assert torch.equal(out, ph)
+    ext0 = torch.zeros((3, 2, plan.N, plan.N), device="cuda")
+    assert torch.equal(plan.reconstruct(s, k, ext_init=ext0).cpu(), zero)
+    plan.set_extension(fwr.EXT_ZERO)
+    assert torch.equal(plan.reconstruct(s, k).cpu(), zero)
+
+
+def test_hudgin_extension_unsupported_paths(fwr):
+    n, pad = 40, 3.2
+    sl, _, mask = synth.batch(n, 1, 3, 0.05)
+    plan = make_plan(fwr, mask, pad, fwr.LSQ)
+    plan.set_extension(fwr.EXT_HUDGIN)
+    plan.set_transform(fwr.TRANSFORM_DFT_BF16X3)
+    with pytest.raises(fwr.FwrError):
+        plan.reconstruct(torch.tensor(sl, dtype=torch.float32, device="cuda"), 1)
+    with pytest.raises(fwr.FwrError):
+        plan.set_extension(2)
