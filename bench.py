@@ -68,8 +68,11 @@ TRAFFIC = {
     "c4cdd161e6b0c782": 18497792,
     # same capture after the P2 twiddles and the P3-input y fill: 12.994 MB + 5.890 MB
     "97a3eb880aeb3f5d": 18883840,
-    # current kernel (compile-time spectral selects, slope prefetch, unrolled set-up): 12.982 MB + 5.505 MB
+    # compile-time spectral selects, slope prefetch, unrolled set-up: 12.982 MB + 5.505 MB
     "b7a334ff342cde75": 18486784,
+    # current kernel (+ the Hudgin-extension instantiation; ncu --metrics dram__bytes_read.sum,
+    # dram__bytes_write.sum, one k = 10 launch of 1000 frames): 12.98 MB + 4.83 MB
+    "da16ea3515ab57b7": 17810000,
 }
 
 

@@ -11,7 +11,9 @@ namespace fwr {
 #include "fwr_fft.cuh"
 #include "fwr_fused.cuh"
 
-template <typename T, int N>
+// HUD: the Hudgin extension as the initial extension (a separate
+// instantiation, so that the default one carries none of its code)
+template <typename T, int N, bool HUD>
 __global__ void __launch_bounds__(4 * N)
 fused_kernel(Params<T> p) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -28,7 +30,8 @@ fused_kernel(Params<T> p) {
                                     p.ext_init ? p.ext_init + size_t(f) * 2 * N * N : nullptr,
                                     p.ext_init_h ? p.ext_init_h + size_t(f) * 2 * N * N : nullptr,
                                     p.phase ? p.phase + size_t(f) * N * N : nullptr,
-                                    p.ext_out ? p.ext_out + size_t(f) * 2 * N * N : nullptr, p.iters, p.hud);
+                                    p.ext_out ? p.ext_out + size_t(f) * 2 * N * N : nullptr, p.iters,
+                                    HUD ? p.hud : nullptr);
         __syncthreads();
     }
     if (!finite) atomicOr(&s_bad, 1);
@@ -129,7 +132,7 @@ cudaError_t launch_n(const Params<T>& p0, cudaStream_t s) {
     Params<T> p = p0;
     p.wf_smem = Layout<T, N>::bytes_wf(p.n) <= size_t(227) * 1024 ? 1 : 0;
     const size_t smem = p.wf_smem ? Layout<T, N>::bytes_wf(p.n) : Layout<T, N>::bytes(p.n);
-    auto kern = fused_kernel<T, N>;
+    auto kern = p.hud ? fused_kernel<T, N, true> : fused_kernel<T, N, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per_sm = 0;

@@ -440,22 +440,30 @@ __device__ __forceinline__ bool fused_frame(const FusedCtx<T, N>& c, const T* sl
     }
     __syncthreads();
 
-    // embed: measurement in the pupil, warm start, Hudgin extension or zero outside
+    if (hud && !warm) {
+        // Hudgin extension staged in Z like a warm start (it needs s0)
+        for (int q = tid; q < N * N; q += NT) {
+            const int row = q / N, col = q % N;
+            Z[row * S + col] = hudgin_cell(s0, ns, hud, n, row - c.off, col - c.off);
+        }
+        __syncthreads();
+    }
+    const bool staged = warm || hud;
+
+    // embed: measurement in the pupil, the staged extension (or zero) outside
     V x[R];
 #pragma unroll
     for (int n1 = 0; n1 < R; ++n1) {
         if (pmask & (1u << n1)) {
             x[n1] = s0row[4 * n1];
-        } else if (warm) {
+        } else if (staged) {
             x[n1] = rowp[4 * n1];
-        } else if (hud) {
-            x[n1] = hudgin_cell(s0, ns, hud, n, r - c.off, 4 * n1 + n2 - c.off);
         } else {
             x[n1] = mk(T(0), T(0));
         }
     }
     // the passes below overwrite Z
-    if (warm) __syncthreads();
+    if (staged) __syncthreads();
 
     for (int it = 0; it <= iters; ++it) {
         const bool final = it == iters;
