@@ -297,20 +297,31 @@ int fwr_plan_grid(const fwr_plan* p) { return p ? p->N : -1; }
 
 int fwr_plan_valid_count(const fwr_plan* p) { return p ? p->nvalid : -1; }
 
-// The plan's filter tables again, for its current measurement model; the
-// device is synchronised first (running launches may read the old tables).
+// The plan's filter tables again, for its current measurement model. The new
+// tables are uploaded first and replace the old ones only when complete (the
+// plan keeps working tables on failure); the device is synchronised before
+// the old ones are freed, since running launches may read them.
 static fwr_status rebuild_tables(fwr_plan* p) {
     int prev = 0;
     cudaGetDevice(&prev);
     cudaSetDevice(p->device);
-    cudaError_t e = cudaDeviceSynchronize();
-    fwr_status st = e == cudaSuccess ? FWR_OK : cuda_fail(e, "synchronise before the table rebuild");
+    HostTables h = build_tables(p->N, p->filter, p->noise_var, p->r0, p->L0, p->g_model, p->pixel);
+    fwr::DevTables<float> t32;
+    fwr::DevTables<double> t64;
+    fwr_status st = upload_tables<float>(h, p->N, t32);
+    if (st == FWR_OK && p->N <= 64) st = upload_tables<double>(h, p->N, t64);
+    if (st == FWR_OK) {
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) st = cuda_fail(e, "synchronise before the table rebuild");
+    }
     if (st == FWR_OK) {
         free_tables(p->f32);
         free_tables(p->f64);
-        HostTables h = build_tables(p->N, p->filter, p->noise_var, p->r0, p->L0, p->g_model, p->pixel);
-        st = upload_tables<float>(h, p->N, p->f32);
-        if (st == FWR_OK && p->N <= 64) st = upload_tables<double>(h, p->N, p->f64);
+        p->f32 = t32;
+        p->f64 = t64;
+    } else {
+        free_tables(t32);
+        free_tables(t64);
     }
     cudaSetDevice(prev);
     return st;
@@ -322,14 +333,20 @@ fwr_status fwr_plan_set_option(fwr_plan* p, int key, double value) {
         const int v = int(value);
         if (double(v) != value || (v != FWR_G_AVERAGED && v != FWR_G_FRIED)) return FWR_ERR_ARG;
         if (v == p->g_model) return FWR_OK;
+        const int old = p->g_model;
         p->g_model = v;
-        return rebuild_tables(p);
+        const fwr_status st = rebuild_tables(p);
+        if (st != FWR_OK) p->g_model = old;
+        return st;
     }
     if (key == FWR_OPT_PIXEL) {
         if (!(value >= 0.0 && value <= 0.5)) return FWR_ERR_ARG;
         if (value == p->pixel) return FWR_OK;
+        const double old = p->pixel;
         p->pixel = value;
-        return rebuild_tables(p);
+        const fwr_status st = rebuild_tables(p);
+        if (st != FWR_OK) p->pixel = old;
+        return st;
     }
     if (key == FWR_OPT_TRANSFORM) {
         const int v = int(value);
