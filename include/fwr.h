@@ -97,9 +97,10 @@ typedef enum {
 #define FWR_PERIODIC_NONE 2            /* never */
 /*
  * Measurement model G of Eq. 4 (Sec. 2); both keys rebuild the plan's filter
- * tables in FP64 (the device is synchronised first, since running launches
- * may read the old tables). Batches and warm starts made from the plan keep
- * the tables they were made with.
+ * tables in FP64. The new tables are uploaded, then the device is
+ * synchronised before the old ones are freed (running launches may read
+ * them); on failure the plan keeps its previous model and tables. Batches and
+ * warm starts made from the plan keep the tables they were made with.
  *   FWR_OPT_G_MODEL: the transverse factor of G, i.e. how a slope averages
  *     across the lenslet. FWR_G_AVERAGED (default): the lenslet-averaged
  *     gradient, Gx = a(u) sinc(v) e^{i pi v}. FWR_G_FRIED: phase known at the
