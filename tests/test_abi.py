@@ -74,3 +74,20 @@ def test_null_plan_calls(lib):
     assert lib.fwr_fft2(48, None, None, 1, 0, None) == 1
     assert lib.fwr_fft2(32, None, None, 0, 0, None) == 0
     lib.fwr_plan_destroy(None)
+
+
+def test_python_constants_match_the_header():
+    """Every #define of include/fwr.h that the binding mirrors has the same
+    value in fwr.py (option keys and their values, filters, limits)."""
+    src = open(os.path.join(ROOT, "include", "fwr.h")).read()
+    defines = {m.group(1): int(m.group(2)) for m in re.finditer(r"#define\s+FWR_([A-Z0-9_]+)\s+(-?\d+)", src)}
+    mirrored = {
+        "OPT_PERIODIC": fwr.OPT_PERIODIC, "OPT_TRANSFORM": fwr.OPT_TRANSFORM, "OPT_G_MODEL": fwr.OPT_G_MODEL,
+        "OPT_PIXEL": fwr.OPT_PIXEL, "OPT_EXTENSION": fwr.OPT_EXTENSION, "G_AVERAGED": fwr.G_AVERAGED,
+        "G_FRIED": fwr.G_FRIED, "EXT_ZERO": fwr.EXT_ZERO, "EXT_HUDGIN": fwr.EXT_HUDGIN,
+        "PERIODIC_BEFORE_EACH_FFT": fwr.PERIODIC_BEFORE_EACH_FFT, "PERIODIC_FINAL_ONLY": fwr.PERIODIC_FINAL_ONLY,
+        "PERIODIC_NONE": fwr.PERIODIC_NONE, "TRANSFORM_FFT": fwr.TRANSFORM_FFT,
+        "TRANSFORM_DFT_BF16X3": fwr.TRANSFORM_DFT_BF16X3,
+    }
+    for name, value in mirrored.items():
+        assert defines.get(name) == value, name
