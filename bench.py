@@ -50,6 +50,11 @@ METRIC = "frames/s at 40x40 lenslets (128² grid), ≤1e-5 rel err vs FP64; lear
 SMS, FP32_LANES, MAX_SM_MHZ = 152, 128, 2070.0
 
 
+# Side outputs of a run (the clocks sampled during the timed region, the
+# autotuner's cache): FWR_BENCH_OUT, else bench_out/ beside this file.
+OUT_DIR = os.environ.get("FWR_BENCH_OUT", os.path.join(ROOT, "bench_out"))
+
+
 def fp32_peak_tflops():
     return SMS * FP32_LANES * 2 * MAX_SM_MHZ * 1e6 / 1e12
 
@@ -98,8 +103,8 @@ class ClockSampler:
 
     def start(self):
         try:
-            os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
-            self.path = os.path.join(ROOT, "gpurun_out", "clocks_gpu%d.csv" % self.gpu)
+            os.makedirs(OUT_DIR, exist_ok=True)
+            self.path = os.path.join(OUT_DIR, "clocks_gpu%d.csv" % self.gpu)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
@@ -262,7 +267,7 @@ def extra_measurements(fwr, synth, torch, flush):
     phases = [torch.empty((plans[pl].N,) * 2, device="cuda") for pl in fp]
     sp, pp = fwr.Batch.pointer_table(slopes), fwr.Batch.pointer_table(phases)
     batch = fwr.Batch(plans, fp, 5)
-    tune_path = os.path.join(ROOT, "gpurun_out", "fwr_tune.jsonl")
+    tune_path = os.path.join(OUT_DIR, "fwr_tune.jsonl")
     os.makedirs(os.path.dirname(tune_path), exist_ok=True)
     ctas, ratio = batch.autotune(sp, pp, tune_path)
     g = torch.cuda.CUDAGraph()
@@ -304,8 +309,8 @@ def extra_measurements(fwr, synth, torch, flush):
 
 
 def measured_bf16_peak():
-    """Dense BF16 tensor peak (TFLOP/s): the measured cuBLAS burst
-    figure when MEASURED_PEAKS.json is present, else the fallback."""
+    """Dense BF16 tensor peak (TFLOP/s): the measured cuBLAS burst figure of
+    MEASURED_PEAKS.json when present, else the fallback."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
             return float(json.load(fh)["bf16_tflops"]), "measured"

@@ -70,7 +70,7 @@ typedef enum {
 typedef enum {
     FWR_OK = 0,
     FWR_ERR_ARG = 1,          /* invalid argument; nothing launched */
-    FWR_ERR_UNSUPPORTED = 2,  /* valid but not supported by this build (grid size, precision) */
+    FWR_ERR_UNSUPPORTED = 2,  /* valid but not supported by the library (grid size, precision, path) */
     FWR_ERR_CUDA = 3,         /* CUDA runtime error (allocation, launch) */
     FWR_ERR_NONFINITE = 4,    /* a measured slope was NaN or Inf (device status) */
     FWR_ERR_TIMEOUT = 5       /* a bounded device wait gave up (device status) */

@@ -14,7 +14,7 @@ It is deliberately slow and literal:
   paper's order, and the final phase comes from the Wiener / least-squares
   filter of Eq. 3.
 
-Conventions (the paper leaves them open; each reading is listed in the design doc):
+Conventions (the paper leaves them open; each is a reading of it):
 
 * Grid index [m, n]: m is the row (y), n the column (x). x slopes are summed
   along a row in Eq. PC, so this matches the paper's s_x(m, n).
