@@ -1,42 +1,10 @@
-"""Pins of the oracle's Hudgin extension (Sec. 3.1): a hand-worked example and
-the closed form for a tilt."""
+"""Pins of the oracle's Hudgin extension (Sec. 3.1): the closed form for a tilt
+and its place in the full path (the hand-worked example is the fixture
+tests/golden/hudgin_6x6.txt, checked in tests/test_golden.py)."""
 
 import numpy as np
 
 import oracle
-
-
-def test_hand_worked_example():
-    # pupil: rows 2-3, columns 1-4, and cell (4, 2); x slopes 10 m + n + 0.5,
-    # y slopes -(10 m + n) - 0.25 on the pupil
-    P = np.zeros((6, 6), bool)
-    P[2:4, 1:5] = True
-    P[4, 2] = True
-    m, n = np.meshgrid(np.arange(6), np.arange(6), indexing="ij")
-    s0x = np.where(P, 10 * m + n + 0.5, 0.0)
-    s0y = np.where(P, -(10 * m + n) - 0.25, 0.0)
-    ex, ey = oracle.hudgin_extension(s0x, s0y, P)
-    # columns: above the top take the top value, below the bottom the bottom
-    # value; columns 0 and 5 have no pupil cells
-    want_x = np.array([
-        [0, 21.5, 22.5, 23.5, 24.5, 0],
-        [0, 21.5, 22.5, 23.5, 24.5, 0],
-        [0, 0, 0, 0, 0, 0],
-        [0, 0, 0, 0, 0, 0],
-        [0, 31.5, 0, 33.5, 34.5, 0],
-        [0, 31.5, 42.5, 33.5, 34.5, 0],
-    ])
-    # rows: left of the first pupil cell its value, right of the last its value
-    want_y = np.array([
-        [0, 0, 0, 0, 0, 0],
-        [0, 0, 0, 0, 0, 0],
-        [-21.25, 0, 0, 0, 0, -24.25],
-        [-31.25, 0, 0, 0, 0, -34.25],
-        [-42.25, -42.25, 0, -42.25, -42.25, -42.25],
-        [0, 0, 0, 0, 0, 0],
-    ])
-    assert np.array_equal(ex, want_x)
-    assert np.array_equal(ey, want_y)
 
 
 def test_tilt_extends_to_every_column_and_row_of_the_pupil():
