@@ -179,15 +179,44 @@ class OraclePool:
 
 
 def cpu_oracle_run(frames_per_core=6):
-    """Bounded sample (about 10 s of CPU work) of the workload on the oracle."""
+    """Bounded sample (about 10 s of CPU work) of the workload on the oracle,
+    and beside it the CPU FFT baseline (cpu_baseline/: the same loop with a
+    radix-2 FFT, FP64 and FP32, one frame per host thread)."""
     pool = OraclePool()
     try:
         n, wall = pool.step(frames_per_core)
     finally:
         pool.close()
-    return {"value": n / wall, "unit": "frames/s", "cores": pool.cores, "kind": "oracle",
-            "sample": "%d frames (%d per core) of the 40x40 -> 128^2 k=%d Wiener workload, FP64 "
-                      "direct-DFT oracle, one process per core" % (n, frames_per_core, ITERS)}
+    res = {"value": n / wall, "unit": "frames/s", "cores": pool.cores, "kind": "oracle",
+           "sample": "%d frames (%d per core) of the 40x40 -> 128^2 k=%d Wiener workload, FP64 "
+                     "direct-DFT oracle, one process per core" % (n, frames_per_core, ITERS)}
+    res["fft_baseline"] = cpu_fft_run()
+    return res
+
+
+def cpu_fft_run(frames_per_thread=16):
+    """The CPU FFT baseline on all host threads, FP64 and FP32, on the
+    benchmark workload's frames (a bounded sample: frames_per_thread each)."""
+    try:
+        import cpu_baseline
+        from paper_1705_04298_gb300 import synth
+        threads = cpu_baseline.threads()
+        F = threads * frames_per_thread
+        r0p, L0p = synth.pitch_units(N_LENSLETS, R0, L0)
+        sl, _, mask = synth.batch(N_LENSLETS, 64, SEED0, SIGMA, R0, L0)
+        sl = np.concatenate([sl] * ((F + 63) // 64))[:F]
+        out = {"kind": "cpu_fft", "unit": "frames/s", "cores": threads,
+               "sample": "%d frames of the 40x40 -> 128^2 k=%d Wiener workload, project-written radix-2 FFT "
+                         "(cpu_baseline/fft_gerchberg.cpp), one frame per thread" % (F, ITERS)}
+        for prec in (64, 32):
+            cpu_baseline.reconstruct(sl[:threads], mask, PAD, ITERS, 1, SIGMA ** 2, r0p, L0p, 0, precision=prec)
+            t0 = time.perf_counter()
+            cpu_baseline.reconstruct(sl, mask, PAD, ITERS, 1, SIGMA ** 2, r0p, L0p, 0, precision=prec)
+            out["fp%d" % prec] = F / (time.perf_counter() - t0)
+        out["value"] = out["fp32"]
+        return out
+    except Exception as e:  # the baseline is context; its absence must not stop the benchmark
+        return {"kind": "cpu_fft", "unavailable": str(e)}
 
 
 # ------------------------------------------------------------------ main ----
@@ -217,8 +246,8 @@ def extra_measurements(fwr, synth, torch, flush):
     256^2 grid with 10 iterations, with the FFT and with the split-BF16
     DFT-as-GEMM transform. The warm starts are measured by
     learned_measurements."""
-    peak = fp32_peak_tflops()
-    res = {}
+    peak, _ = fwr.fp32_fma_peak()
+    res = {"fp32_peak_tflops_measured": peak}
     # 40x40 on 128^2, k in {0, 1, 2, 5}
     sl, _, mask = synth.batch(N_LENSLETS, FRAMES, SEED0, SIGMA, R0, L0)
     r0p, L0p = synth.pitch_units(N_LENSLETS, R0, L0)
@@ -471,6 +500,74 @@ def run_reference(args):
     return 0
 
 
+WORKLOADS = ("fused128", "slab256", "dftgemm256", "unet", "linws")
+
+
+def run_workload(args):
+    """One of the path's workloads, run --reps times after one warm-up call
+    and timed with CUDA events (mean; no L2 flush): the command that the
+    profile summaries capture under ncu. Each is a plain sequence of library
+    calls on seeded synthetic frames (--frames, 1000 by default):
+      fused128    40x40 lenslets on 128^2, Wiener, --iters iterations
+      slab256     128x128 lenslets on 256^2 (frozen-flow frames), LSQ, --iters
+      dftgemm256  the same through the split-BF16 DFT-as-GEMM transform
+      unet        the warm-start U-Net forward on 40x40 slopes (committed weights)
+      linws       the linear warm start (--rank) alone, then with --iters
+                  iterations (fwr_linws_forward, fwr_linws_reconstruct)
+    """
+    import torch
+    from paper_1705_04298_gb300 import fwr, learned, synth
+    fwr.load()
+    F, k = args.frames, args.iters
+    runs = []
+    if args.workload == "fused128":
+        sl, _, mask = synth.batch(40, min(F, 64), SEED0, SIGMA)
+        r0p, L0p = synth.pitch_units(40, R0, L0)
+        plan = fwr.Plan(mask, PAD, fwr.WIENER, SIGMA ** 2, r0p, L0p)
+        s = torch.tensor(sl, dtype=torch.float32, device="cuda").repeat((F + 63) // 64, 1, 1, 1)[:F].contiguous()
+        out = torch.empty((F, plan.N, plan.N), device="cuda")
+        runs.append(("fused128_k%d" % k, lambda: plan.reconstruct(s, k, out)))
+    elif args.workload in ("slab256", "dftgemm256"):
+        sl, _, mask = synth.frozen_flow(128, 32, 7, 0.05, r0=0.12, L0=25.0)
+        plan = fwr.Plan(mask, 2.0, fwr.LSQ)
+        if args.workload == "dftgemm256":
+            plan.set_transform(fwr.TRANSFORM_DFT_BF16X3)
+        s = torch.tensor(sl, dtype=torch.float32, device="cuda").repeat((F + 31) // 32, 1, 1, 1)[:F].contiguous()
+        out = torch.empty((F, plan.N, plan.N), device="cuda")
+        runs.append(("%s_k%d" % (args.workload, k), lambda: plan.reconstruct(s, k, out)))
+    elif args.workload == "unet":
+        net = learned.load_net(fwr, learned.WEIGHTS, max_batch=F)
+        plan = learned.make_plan(fwr, fwr.WIENER, learned.EVAL_SIGMA)
+        s, _ = learned.frames(F, learned.EVAL_SEED0, learned.EVAL_SIGMA)
+        out = torch.empty((F, 2, 128, 128), device="cuda")
+        runs.append(("unet_forward", lambda: net.forward(plan, s, out)))
+    else:
+        from paper_1705_04298_gb300 import linws
+        mask = synth.pupil_mask(learned.N_LENSLETS)
+        plan = learned.make_plan(fwr, fwr.WIENER, learned.EVAL_SIGMA)
+        ws, _ = linws.build(fwr, plan, mask, args.rank, max_batch=F, frames=1024, log=None)
+        s, _ = learned.frames(F, learned.EVAL_SEED0, learned.EVAL_SIGMA)
+        warm = torch.empty((F, 2, 128, 128), device="cuda")
+        out = torch.empty((F, 128, 128), device="cuda")
+        runs.append(("linws_r%d_forward" % args.rank, lambda: ws.forward(s, warm)))
+        runs.append(("linws_r%d_reconstruct_k%d" % (args.rank, k), lambda: ws.reconstruct(s, k, out)))
+    res = {}
+    for name, run in runs:
+        run()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.reps):
+            run()
+        e1.record()
+        torch.cuda.synchronize()
+        res[name + "_ms"] = e0.elapsed_time(e1) / args.reps
+    res["frames"] = F
+    print(json.dumps(res), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -480,9 +577,16 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--iters", type=int, default=ITERS)
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--workload", choices=WORKLOADS, default=None,
+                    help="run one workload --reps times (for profiling) instead of the benchmark")
+    ap.add_argument("--frames", type=int, default=FRAMES)
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--rank", type=int, default=256, help="rank of the linws workload")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload:
+        return run_workload(args)
 
     rank, world, local = dist_env()
     cpu_base = None
@@ -515,6 +619,8 @@ def main():
     for _ in range(args.warmup):
         plan.reconstruct(slopes, k, phase)
     torch.cuda.synchronize()
+    # the roofline's denominator: measured FP32 FMA throughput of this GPU
+    peak_meas, _ = fwr.fp32_fma_peak()
 
     clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
@@ -563,7 +669,7 @@ def main():
     if rank == 0:
         fl = flops_per_frame(N, k) * FRAMES
         achieved = fl / (ms_per_step / 1000.0) / 1e12
-        peak = fp32_peak_tflops()
+        peak = peak_meas
         src = kernel_source_hash()
         line = {
             "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world,
@@ -578,7 +684,9 @@ def main():
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": TRAFFIC.get(src),
                          "kernel": "fused_kernel<float,128>", "flops_per_launch": fl,
-                         "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 x 2.07 GHz (max SM clock)",
+                         "peak_source": "measured: fwr_fp32_fma_peak (FP32 FMA throughput, burst, this GPU)",
+                         "peak_derived": fp32_peak_tflops(), "frac_of_derived": achieved / fp32_peak_tflops(),
+                         "peak_derived_note": "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (max SM clock)",
                          "source_hash": src},
             "e2e": {"value": FRAMES * world / (e2e_step / 1000.0), "unit": "frames/s",
                     "h2d_bytes_per_step": int(sh.numel() * 4), "d2h_bytes_per_step": int(ph_host.numel() * 4)},

@@ -119,7 +119,7 @@ typedef enum {
 /*
  * FWR_OPT_EXTENSION: the slopes outside the pupil before the first iteration
  * when no warm start is passed. FWR_EXT_ZERO (default): zero. FWR_EXT_HUDGIN:
- * the Hudgin extension of Sec. 3.1 (after Poyneer et al.): every x slope
+ * the Hudgin extension of Sec. 3.2 (after Poyneer et al.): every x slope
  * outside the pupil takes the measured x slope at the top or bottom pupil
  * edge of its column (up or down to the grid edge), every y slope the
  * measured y slope at the left or right pupil edge of its row; gaps inside a
@@ -273,6 +273,39 @@ double fwr_batch_cost_ratio(const fwr_batch* batch);
 void fwr_batch_destroy(fwr_batch* batch);
 
 /*
+ * One-call ragged reconstruction: every frame f goes through plan
+ * plans[frame_plan_dev[f]] (Algorithm 1 and Eqs. 2-3 per frame, as
+ * fwr_reconstruct), all frames in ONE persistent kernel launch on `stream`.
+ *   plans           HOST array of n_plans plans on one device, each N = 128
+ *                   (n <= 85) or N = 256 (FWR_ERR_UNSUPPORTED otherwise)
+ *   frame_plan_dev  DEVICE int array [n_frames] of plan indices
+ *   slopes_dev      DEVICE array of n_frames device pointers, frame f's
+ *                   [2][n][n] floats of its plan
+ *   phase_dev       DEVICE array of n_frames device pointers to [N][N]
+ *                   floats (16-byte aligned)
+ *   iters           Gerchberg iterations of every frame, 0..64
+ * The schedule (frames per CTA, longest first, grouped by plan; the batch
+ * object above with its default schedule) is built on the first call for a
+ * given (plans, their tables and periodic modes, frame_plan_dev, n_frames,
+ * iters) and kept: that first call reads frame_plan_dev after the caller's
+ * earlier work on `stream` (synchronising it), validates every index
+ * (FWR_ERR_ARG) and allocates the schedule and, with a 256x256 plan, 512 KB
+ * of working memory per SM. Later calls with the same key allocate nothing
+ * and do not synchronise (CUDA-graph capturable). The kernel reads each
+ * frame's plan from frame_plan_dev at run time, so rewriting its contents
+ * keeps results correct (only the load balance is the first call's); a frame
+ * whose index has become invalid is skipped and sets FWR_ERR_ARG in the
+ * status word of plans[0] (fwr_get_status). Calls with one key must not
+ * overlap on the GPU (shared working memory). The plans must outlive the
+ * kept schedules: fwr_ragged_release frees all of them (synchronises the
+ * devices through cudaFree).
+ */
+fwr_status fwr_reconstruct_ragged(fwr_plan* const* plans, int n_plans, const int* frame_plan_dev,
+                                  const float* const* slopes_dev, int n_frames, int iters,
+                                  float* const* phase_dev, void* stream);
+void fwr_ragged_release(void);
+
+/*
  * Learned warm start (the paper has no learned component; this is the
  * project's addition). A small U-Net predicts the slopes outside the pupil
  * from the measured ones; passed as ext_init to fwr_reconstruct_ex it lets
@@ -352,21 +385,26 @@ fwr_status fwr_schedule_lpt(const double* costs, int n, int ctas, int* cta_off, 
  * plan is created). This entry point instead uses an array that is part of
  * the library itself: room for FWR_STATIC_SCRATCH_GRIDS frames in flight
  * (8 MB), present on every GPU that loads the library until the process
- * exits. It calls no cudaMalloc or cudaFree.
+ * exits. It calls no cudaMalloc or cudaFree, and loads nothing: creating a
+ * 256x256 plan loads the library's device code on the plan's device and
+ * looks up the array's address there, so do that at start-up (a plan made
+ * before a cudaDeviceReset is unusable after it, like all its memory).
  *
- *   plan          a plan with N = 256 (FWR_ERR_UNSUPPORTED otherwise)
+ *   plan          a plan with N = 256 and the shared-memory FFT transform
+ *                 (FWR_ERR_UNSUPPORTED otherwise: other grids have no scratch,
+ *                 and FWR_TRANSFORM_DFT_BF16X3 has its own workspace)
  *   slopes_dev, n_frames, iters, phase_dev, stream   as for fwr_reconstruct
  *   ctas          frames processed concurrently, 1 .. FWR_STATIC_SCRATCH_GRIDS
  *                 (FWR_ERR_ARG otherwise; fwr_last_error() says why); any
  *                 n_frames is accepted, the CTAs loop over the frames
  *
- * The results equal fwr_reconstruct's. The array is shared by all calls on a
- * device and keeps the last call's contents; nothing in it needs to start at
- * zero, because every frame writes its whole area before reading it. Calls
- * that overlap on the GPU (other streams, other threads, other plans) race on
- * the array: serialise them. The first call on each device looks up the
- * array's device address (cudaGetSymbolAddress) with that device current;
- * make that first call before any stream capture.
+ * The kernel is fwr_reconstruct's, on the same tables and options (periodic
+ * mode, measurement model, Hudgin extension), so the results are bitwise
+ * equal to fwr_reconstruct's. The array is shared by all calls on a device and
+ * keeps the last call's contents; nothing in it needs to start at zero,
+ * because every frame writes its whole area before reading it. Calls that
+ * overlap on the GPU (other streams, other threads, other plans) race on the
+ * array: serialise them.
  */
 #define FWR_STATIC_SCRATCH_GRIDS 16
 fwr_status fwr_reconstruct_static(fwr_plan* plan, const float* slopes_dev, int n_frames, int iters,
@@ -393,7 +431,8 @@ fwr_status fwr_dft2_bf16x3(int N, const float* in_dev, float* out_dev, int n_fra
 
 /*
  * Read and clear the plan's sticky device status word. Synchronises the
- * plan's device. FWR_OK, FWR_ERR_NONFINITE or FWR_ERR_TIMEOUT.
+ * plan's device. FWR_OK, FWR_ERR_NONFINITE, FWR_ERR_TIMEOUT or (ragged
+ * launches given an invalid plan index) FWR_ERR_ARG.
  */
 fwr_status fwr_get_status(fwr_plan* plan);
 
@@ -446,6 +485,26 @@ fwr_status fwr_linws_reconstruct(fwr_linws* ws, fwr_plan* plan, const float* slo
                                  int iters, float* phase_dev, void* stream);
 fwr_status fwr_linws_status(fwr_linws* ws);
 fwr_status fwr_gemm_bf16_tc(const void* A_dev, const void* B_dev, int M, int N, int K, float* D_dev, void* stream);
+/*
+ * fwr_gemm_bf16_tc with the MMA issuer's and the epilogue's mbarrier waits
+ * bounded by wait_cycles (1 .. 4e9 SM clock cycles; fwr_gemm_bf16_tc uses
+ * 4e9, about two seconds) instead of the default. For testing the timeout
+ * path: with a few cycles the issuer gives up before the first operand tiles
+ * land, the kernel drains its loads in flight (those waits keep the full
+ * bound), frees its tensor memory and the call returns FWR_ERR_TIMEOUT with
+ * the context intact. D is then undefined.
+ */
+fwr_status fwr_gemm_bf16_tc_limit(const void* A_dev, const void* B_dev, int M, int N, int K, float* D_dev,
+                                  long long wait_cycles, void* stream);
+
+/*
+ * Measured FP32 FMA throughput of the current device, the peak of the FFT
+ * path's roofline: 2 CTAs of 512 threads per SM, each thread 8 independent
+ * FMA chains, best of five timed launches (about 2 ms each) after a warm-up,
+ * synchronous on `stream`. *tflops = 2 x FMAs / time in TFLOP/s; *ms (may be
+ * NULL) the launch time.
+ */
+fwr_status fwr_fp32_fma_peak(double* tflops, double* ms, void* stream);
 
 /* Static, human-readable name of a status code. */
 const char* fwr_status_string(fwr_status status);

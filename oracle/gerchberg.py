@@ -235,7 +235,7 @@ def embed(slopes, mask, N):
 
 
 def hudgin_extension(s0x, s0y, P):
-    """The Hudgin extension of Sec. 3.1 (from Poyneer et al.): outside the
+    """The Hudgin extension of Sec. 3.2 (from Poyneer et al.): outside the
     pupil, every x slope takes the measured x slope at the top or bottom edge
     of the pupil in its column (the nearer end, going up or down to the grid
     edge), and every y slope the measured y slope at the left or right edge of

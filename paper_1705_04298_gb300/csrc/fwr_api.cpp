@@ -261,6 +261,13 @@ fwr_status fwr_plan_create(fwr_plan** out, int n, double pad_factor, const uint8
             p->scratch_ctas = fwr::slab_max_ctas();
             const size_t b = size_t(p->scratch_ctas) * fwr::slab_scratch_elems_per_cta() * sizeof(float2);
             if ((e = cudaMalloc(&p->d_scratch, b)) != cudaSuccess) st = cuda_fail(e, "cudaMalloc scratch");
+            // the static array of fwr_reconstruct_static: its address on this
+            // device, looked up now so that the allocation-free call itself
+            // loads nothing; a failure here only disables that entry point
+            if (st == FWR_OK && fwr::static_slab_prepare(n, &p->d_static_scratch) != cudaSuccess) {
+                p->d_static_scratch = nullptr;
+                cudaGetLastError();
+            }
         }
     }
     if (st != FWR_OK) {
@@ -458,11 +465,23 @@ fwr_status fwr_reconstruct_static(fwr_plan* p, const float* slopes, int n_frames
                       "fwr_reconstruct_static: only 256x256 grids use scratch memory (plan grid is %d)", p->N);
         return FWR_ERR_UNSUPPORTED;
     }
+    if (p->transform != FWR_TRANSFORM_FFT) {
+        std::snprintf(g_last_error, sizeof(g_last_error),
+                      "fwr_reconstruct_static: only the shared-memory FFT transform uses the static scratch "
+                      "(the plan's FWR_OPT_TRANSFORM is %d)", p->transform);
+        return FWR_ERR_UNSUPPORTED;
+    }
     if (ctas < 1 || ctas > FWR_STATIC_SCRATCH_GRIDS) {
         std::snprintf(g_last_error, sizeof(g_last_error),
                       "fwr_reconstruct_static: ctas = %d, the static scratch holds 1..%d grids of 256x256", ctas,
                       FWR_STATIC_SCRATCH_GRIDS);
         return FWR_ERR_ARG;
+    }
+    if (!p->d_static_scratch) {
+        std::snprintf(g_last_error, sizeof(g_last_error),
+                      "fwr_reconstruct_static: the static scratch's device address could not be looked up when the "
+                      "plan was created");
+        return FWR_ERR_CUDA;
     }
     if (n_frames == 0) return FWR_OK;
     fwr::Params<float> k;
@@ -479,7 +498,7 @@ fwr_status fwr_reconstruct_static(fwr_plan* p, const float* slopes, int n_frames
     k.periodic = p->periodic;
     k.status = p->d_status;
     if (p->extension == FWR_EXT_HUDGIN) k.hud = p->d_hud;
-    cudaError_t e = fwr::launch_slab_static(k, ctas, static_cast<cudaStream_t>(stream));
+    cudaError_t e = fwr::launch_slab_static(k, p->d_static_scratch, ctas, static_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? FWR_OK : cuda_fail(e, "static-scratch launch");
 }
 
@@ -658,6 +677,7 @@ fwr_status fwr_get_status(fwr_plan* p) {
     if (e != cudaSuccess) return cuda_fail(e, "status read");
     if (v & fwr::STATUS_NONFINITE) return FWR_ERR_NONFINITE;
     if (v & fwr::STATUS_TIMEOUT) return FWR_ERR_TIMEOUT;
+    if (v & fwr::STATUS_BADINDEX) return FWR_ERR_ARG;
     return FWR_OK;
 }
 

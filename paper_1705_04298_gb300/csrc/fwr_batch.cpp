@@ -12,7 +12,10 @@
 #include <cstring>
 #include <fstream>
 #include <functional>
+#include <map>
+#include <mutex>
 #include <new>
+#include <tuple>
 #include <queue>
 #include <sstream>
 #include <string>
@@ -190,21 +193,28 @@ fwr_status fwr_batch_schedule(fwr_batch* b, int ctas, double cost_ratio) {
     return FWR_OK;
 }
 
-fwr_status fwr_batch_run(fwr_batch* b, const float* const* slopes_dev, float* const* phase_dev, void* stream) {
+static fwr_status batch_run(fwr_batch* b, const int* frame_plan_dev, const float* const* slopes_dev,
+                            float* const* phase_dev, void* stream) {
     if (!b) return FWR_ERR_ARG;
     if (b->n_frames == 0) return FWR_OK;
     if (!slopes_dev || !phase_dev) return FWR_ERR_ARG;
     fwr::RaggedParams p;
     p.plans = b->d_plans;
-    p.frame_plan = b->d_frame_plan;
+    p.frame_plan = frame_plan_dev;
     p.cta_off = b->d_off;
     p.order = b->d_order;
     p.slopes = slopes_dev;
     p.phase = phase_dev;
     p.scratch = b->d_scratch;
     p.iters = b->iters;
+    p.n_plans = int(b->plans.size());
     cudaError_t e = fwr::launch_ragged(p, b->ctas, b->smem, static_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? FWR_OK : fwr::cuda_fail(e, "ragged launch");
+}
+
+fwr_status fwr_batch_run(fwr_batch* b, const float* const* slopes_dev, float* const* phase_dev, void* stream) {
+    if (!b) return FWR_ERR_ARG;
+    return batch_run(b, b->d_frame_plan, slopes_dev, phase_dev, stream);
 }
 
 int fwr_batch_ctas(const fwr_batch* b) { return b ? b->ctas : -1; }
@@ -305,6 +315,75 @@ fwr_status fwr_batch_autotune(fwr_batch* b, const float* const* slopes_dev, floa
           << ", \"ms_per_run\": " << best_ms / 3.0 << "}\n";
     }
     return st;
+}
+
+}  // extern "C"
+
+// One-call ragged entry point: a schedule per (plans and their tables, frame
+// table, frame count, iterations), built on first use and kept until
+// fwr_ragged_release.
+namespace {
+
+struct RaggedKey {
+    int device;
+    std::vector<uintptr_t> plans;  // plan, its FP32 table, periodic mode, per plan
+    uintptr_t frame_plan;
+    int n_frames, iters;
+    bool operator<(const RaggedKey& o) const {
+        return std::tie(device, plans, frame_plan, n_frames, iters) <
+               std::tie(o.device, o.plans, o.frame_plan, o.n_frames, o.iters);
+    }
+};
+
+std::mutex g_ragged_mu;
+std::map<RaggedKey, fwr_batch*> g_ragged;
+
+}  // namespace
+
+extern "C" {
+
+fwr_status fwr_reconstruct_ragged(fwr_plan* const* plans, int n_plans, const int* frame_plan_dev,
+                                  const float* const* slopes_dev, int n_frames, int iters, float* const* phase_dev,
+                                  void* stream) {
+    if (!plans || n_plans < 1 || n_frames < 0 || iters < 0 || iters > 64) return FWR_ERR_ARG;
+    if (n_frames == 0) return FWR_OK;
+    if (!frame_plan_dev || !slopes_dev || !phase_dev) return FWR_ERR_ARG;
+    RaggedKey key;
+    key.device = plans[0] ? plans[0]->device : -1;
+    for (int i = 0; i < n_plans; ++i) {
+        const fwr_plan* p = plans[i];
+        if (!p) return FWR_ERR_ARG;
+        key.plans.push_back(reinterpret_cast<uintptr_t>(p));
+        key.plans.push_back(reinterpret_cast<uintptr_t>(p->f32.iota));
+        key.plans.push_back(uintptr_t(p->periodic));
+    }
+    key.frame_plan = reinterpret_cast<uintptr_t>(frame_plan_dev);
+    key.n_frames = n_frames;
+    key.iters = iters;
+    std::lock_guard<std::mutex> lock(g_ragged_mu);
+    auto it = g_ragged.find(key);
+    fwr_batch* b = nullptr;
+    if (it != g_ragged.end()) {
+        b = it->second;
+    } else {
+        // first call for this key: read the frame table (ordered after the
+        // caller's earlier work on `stream`), build and keep the schedule
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        std::vector<int> fp(n_frames);
+        cudaError_t e = cudaMemcpyAsync(fp.data(), frame_plan_dev, sizeof(int) * n_frames, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return fwr::cuda_fail(e, "fwr_reconstruct_ragged: frame table");
+        fwr_status st = fwr_batch_create(&b, plans, n_plans, fp.data(), n_frames, iters);
+        if (st != FWR_OK) return st;
+        g_ragged[key] = b;
+    }
+    return batch_run(b, frame_plan_dev, slopes_dev, phase_dev, stream);
+}
+
+void fwr_ragged_release(void) {
+    std::lock_guard<std::mutex> lock(g_ragged_mu);
+    for (auto& kv : g_ragged) fwr_batch_destroy(kv.second);
+    g_ragged.clear();
 }
 
 }  // extern "C"

@@ -45,7 +45,7 @@ template <typename T> struct Params {
 enum : int { PERIODIC_BEFORE_EACH_FFT = 0, PERIODIC_FINAL_ONLY = 1, PERIODIC_NONE = 2 };
 
 // Status bits written by kernels.
-enum : unsigned { STATUS_NONFINITE = 1u, STATUS_TIMEOUT = 2u };
+enum : unsigned { STATUS_NONFINITE = 1u, STATUS_TIMEOUT = 2u, STATUS_BADINDEX = 4u };
 
 // Shared-memory bytes of the generic kernel (fwr_basic.cu) for grid N.
 size_t basic_smem_bytes(int N, int elem_bytes, int n);
@@ -69,9 +69,12 @@ int slab_max_ctas();
 cudaError_t launch_slab(const Params<float>& p, float2* scratch, int max_ctas, cudaStream_t s);
 // The same kernel on the library's static scratch array (no allocation):
 // at most STATIC_SLAB_GRIDS CTAs; cudaErrorInvalidValue for ctas outside
-// 1..STATIC_SLAB_GRIDS.
+// 1..STATIC_SLAB_GRIDS. static_slab_prepare (current device) returns the
+// array's device address and sets the kernel's shared-memory limit for n
+// lenslets; launch_slab_static takes that address.
 enum : int { STATIC_SLAB_GRIDS = 16 };
-cudaError_t launch_slab_static(const Params<float>& p, int ctas, cudaStream_t s);
+cudaError_t static_slab_prepare(int n, float2** addr);
+cudaError_t launch_slab_static(const Params<float>& p, float2* scratch, int ctas, cudaStream_t s);
 
 // Ragged batches (fwr_ragged.cu): one launch over frames of several plans
 // with N in {128, 256}. cta_off[grid + 1] / order[] list each CTA's frames;
@@ -91,6 +94,7 @@ struct RaggedParams {
     float* const* phase;
     float2* scratch;  // grid x 256^2 (only when a 256^2 plan is present)
     int iters;
+    int n_plans;      // frames whose plan index is outside 0..n_plans-1 are skipped (STATUS_BADINDEX)
 };
 size_t ragged_smem_bytes(int N, int n);  // 0 if the plan cannot join a ragged batch
 cudaError_t ragged_prepare(size_t smem);

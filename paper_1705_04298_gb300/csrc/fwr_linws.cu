@@ -94,7 +94,8 @@ int device_sms(int device) {
 // when N allows them and they still give every SM a tile, else 128-wide.
 template <typename OutT>
 cudaError_t launch_gemm(const CUtensorMap& ma, const CUtensorMap& mb128, const CUtensorMap& mb256, int M,
-                        long long N, int K, OutT* D, long long ldd, int* status, cudaStream_t s) {
+                        long long N, int K, OutT* D, long long ldd, int* status, cudaStream_t s,
+                        long long wait_limit = fwr::umma::WAIT_LIMIT) {
     int dev = 0;
     cudaGetDevice(&dev);
     const int sms = device_sms(dev);
@@ -106,11 +107,11 @@ cudaError_t launch_gemm(const CUtensorMap& ma, const CUtensorMap& mb128, const C
     if (bn == 256)
         fwr::umma::gemm_kernel<256, GEMM_BK, OutT>
             <<<grid, fwr::umma::THREADS, fwr::umma::Cfg<256, GEMM_BK>::SMEM, s>>>(ma, mb256, M, int(N), K, D, ldd,
-                                                                              status);
+                                                                              status, wait_limit);
     else
         fwr::umma::gemm_kernel<128, GEMM_BK, OutT>
             <<<grid, fwr::umma::THREADS, fwr::umma::Cfg<128, GEMM_BK>::SMEM, s>>>(ma, mb128, M, int(N), K, D, ldd,
-                                                                              status);
+                                                                              status, wait_limit);
     return cudaGetLastError();
 }
 
@@ -224,6 +225,13 @@ bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) ==
 extern "C" {
 
 fwr_status fwr_gemm_bf16_tc(const void* A, const void* B, int M, int N, int K, float* D, void* stream) {
+    return fwr_gemm_bf16_tc_limit(A, B, M, N, K, D, fwr::umma::WAIT_LIMIT, stream);
+}
+
+fwr_status fwr_gemm_bf16_tc_limit(const void* A, const void* B, int M, int N, int K, float* D, long long wait_cycles,
+                                  void* stream) {
+    if (wait_cycles < 1 || wait_cycles > fwr::umma::WAIT_LIMIT)
+        return fail(FWR_ERR_ARG, "fwr_gemm_bf16_tc_limit: wait_cycles outside 1 .. 4e9");
     if (M < 0 || N < 0 || K < 0) return fail(FWR_ERR_ARG, "fwr_gemm_bf16_tc: negative size");
     if (M == 0 || N == 0) return FWR_OK;
     if (K < 1 || K % 8 != 0 || N % 128 != 0)
@@ -239,7 +247,7 @@ fwr_status fwr_gemm_bf16_tc(const void* A, const void* B, int M, int N, int K, f
     int* st = nullptr;
     cudaError_t e = cudaMalloc(&st, sizeof(int));
     if (e == cudaSuccess) e = cudaMemsetAsync(st, 0, sizeof(int), s);
-    if (e == cudaSuccess) e = launch_gemm<float>(ma, mb128, mb256, M, N, K, D, N, st, s);
+    if (e == cudaSuccess) e = launch_gemm<float>(ma, mb128, mb256, M, N, K, D, N, st, s, wait_cycles);
     int h = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&h, st, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);

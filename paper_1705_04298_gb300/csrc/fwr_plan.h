@@ -57,6 +57,9 @@ struct fwr_plan {
     fwr::DevTables<double> f64;
     // 256^2 grids: per-CTA global scratch of the slab kernel
     float2* d_scratch = nullptr;
+    // 256^2 grids: device address of the library's static scratch array on the
+    // plan's device (looked up at plan creation; nullptr if that failed)
+    float2* d_static_scratch = nullptr;
     // DFT-as-GEMM transform on 128^2 / 256^2 grids: operands and chunk buffers
     void* d_dftws = nullptr;
     int scratch_ctas = 0;

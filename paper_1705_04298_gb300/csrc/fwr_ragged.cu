@@ -31,6 +31,11 @@ ragged_kernel(RaggedParams rp) {
     for (int i = i0; i < i1; ++i) {
         const int f = rp.order[i];
         const int pl = rp.frame_plan[f];
+        if (pl < 0 || pl >= rp.n_plans) {
+            // a frame table rewritten with an invalid index: skip the frame
+            if (threadIdx.x == 0) atomicOr(rp.plans[0].status, STATUS_BADINDEX);
+            continue;
+        }
         const RaggedPlan P = rp.plans[pl];
         if (pl != cur) {
             if (P.N == 128) fused_setup<float, 128>(fc, smem, P.tab, P.mask, P.n, P.off, P.periodic);

@@ -4,8 +4,6 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include <mutex>
-
 #include "fwr_internal.h"
 
 namespace fwr {
@@ -62,32 +60,23 @@ cudaError_t launch_slab(const Params<float>& p, float2* scratch, int max_ctas, c
 // ---------------------------------------------------------------------------
 static __device__ __align__(256) float2 g_static_slab_scratch[STATIC_SLAB_GRIDS * SN * SN];
 
-cudaError_t launch_slab_static(const Params<float>& p, int ctas, cudaStream_t s) {
-    if (ctas < 1 || ctas > STATIC_SLAB_GRIDS) return cudaErrorInvalidValue;
-    // Host code cannot use the array's name as a device address: look the
-    // address up once per device, with that device current, and cache it.
-    static std::mutex mu;
-    static float2* addr[64] = {};
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+// Host code cannot use the array's name as a device address: look the address
+// up with the device current (this also loads the module on that device, so a
+// later call does no loading) and set the kernel's shared-memory limit.
+cudaError_t static_slab_prepare(int n, float2** addr) {
+    void* ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_slab_scratch);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    float2* scratch = nullptr;
-    {
-        std::lock_guard<std::mutex> lock(mu);
-        if (!addr[dev]) {
-            void* ptr = nullptr;
-            e = cudaGetSymbolAddress(&ptr, g_static_slab_scratch);
-            if (e != cudaSuccess) return e;
-            addr[dev] = static_cast<float2*>(ptr);
-        }
-        scratch = addr[dev];
-    }
-    const size_t smem = slab_smem_bytes(p.n);
-    e = cudaFuncSetAttribute(slab_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    e = cudaFuncSetAttribute(slab_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(slab_smem_bytes(n)));
     if (e != cudaSuccess) return e;
+    *addr = static_cast<float2*>(ptr);
+    return cudaSuccess;
+}
+
+cudaError_t launch_slab_static(const Params<float>& p, float2* scratch, int ctas, cudaStream_t s) {
+    if (ctas < 1 || ctas > STATIC_SLAB_GRIDS || !scratch) return cudaErrorInvalidValue;
     const int grid = ctas < p.F ? ctas : p.F;
-    slab_kernel<<<grid, SNT, smem, s>>>(p, scratch);
+    slab_kernel<<<grid, SNT, slab_smem_bytes(p.n), s>>>(p, scratch);
     return cudaGetLastError();
 }
 

@@ -91,12 +91,14 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait on phase `parity`; false when the CTA aborted or the limit ran out.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort) {
+// Bounded wait on phase `parity`; false when the CTA aborted or `limit`
+// cycles ran out.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort,
+                                          long long limit = WAIT_LIMIT) {
     const long long t0 = clock64();
     while (!mbar_try(bar, parity)) {
         if (*abort) return false;
-        if (clock64() - t0 > WAIT_LIMIT) {
+        if (clock64() - t0 > limit) {
             *abort = 1;
             return false;
         }
@@ -229,10 +231,13 @@ __device__ __forceinline__ void mbar_drain(uint32_t bar, uint32_t parity, volati
 // D[M][ldd] = A B^T over K, N a multiple of BN. The maps describe A as {K, M}
 // with box {64, 128} and B as {K, N} with box {64, BN}; K beyond the tensors'
 // extent and rows beyond M read as zeros (TMA fill) and are not stored.
+// wait_limit bounds the MMA issuer's and the epilogue's waits (WAIT_LIMIT in
+// normal use; a test passes a few cycles to make them run out); the
+// producer's waits and every drain of work in flight keep WAIT_LIMIT.
 template <int BN, int BK, typename OutT>
 __global__ void __launch_bounds__(THREADS, 1)
     gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int M, int N,
-                int K, OutT* __restrict__ D, long long ldd, int* status) {
+                int K, OutT* __restrict__ D, long long ldd, int* status, long long wait_limit) {
     typedef Cfg<BN, BK> C;
     constexpr int S = C::STAGES;
     extern __shared__ uint8_t smem_raw[];
@@ -306,12 +311,12 @@ __global__ void __launch_bounds__(THREADS, 1)
             bool ok = true;
             for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++jt) {
                 const int b = jt & 1, ub = jt >> 1;
-                if (ub > 0 && !mbar_wait(acce0 + 8 * b, uint32_t(ub - 1) & 1u, abort)) break;
+                if (ub > 0 && !mbar_wait(acce0 + 8 * b, uint32_t(ub - 1) & 1u, abort, wait_limit)) break;
                 fence_after();
                 const uint32_t d = tmem + uint32_t(b * BN);
                 for (int kb = 0; kb < kblocks; ++kb, ++it) {
                     const int s = it % S, use = it / S;
-                    if (!mbar_wait(full0 + 8 * s, uint32_t(use) & 1u, abort)) {
+                    if (!mbar_wait(full0 + 8 * s, uint32_t(use) & 1u, abort, wait_limit)) {
                         ok = false;
                         break;
                     }
@@ -336,7 +341,8 @@ __global__ void __launch_bounds__(THREADS, 1)
         int jt = 0;
         for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++jt) {
             const int b = jt & 1, ub = jt >> 1;
-            const bool ok = __all_sync(0xffffffffu, mbar_wait(accf0 + 8 * b, uint32_t(ub) & 1u, abort) && !*abort);
+            const bool ok =
+                __all_sync(0xffffffffu, mbar_wait(accf0 + 8 * b, uint32_t(ub) & 1u, abort, wait_limit) && !*abort);
             if (!ok) break;
             fence_after();
             const int m0 = (t % tiles_m) * BM, n0 = (t / tiles_m) * BN;

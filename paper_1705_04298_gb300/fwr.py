@@ -65,6 +65,8 @@ SIGNATURES = {
     "fwr_batch_cost_ratio": (_D, [_P]),
     "fwr_batch_destroy": (None, [_P]),
     "fwr_schedule_lpt": (_I, [_P, _I, _I, _P, _P]),
+    "fwr_reconstruct_ragged": (_I, [_P, _I, _P, _P, _I, _I, _P, _P]),
+    "fwr_ragged_release": (None, []),
     "fwr_net_create": (_I, [ctypes.POINTER(_P), _I, _I, _P, _I]),
     "fwr_net_destroy": (None, [_P]),
     "fwr_net_param_count": (_I, [_P]),
@@ -82,7 +84,9 @@ SIGNATURES = {
     "fwr_linws_reconstruct": (_I, [_P, _P, _P, _I, _I, _P, _P]),
     "fwr_linws_status": (_I, [_P]),
     "fwr_gemm_bf16_tc": (_I, [_P, _P, _I, _I, _I, _P, _P]),
+    "fwr_gemm_bf16_tc_limit": (_I, [_P, _P, _I, _I, _I, _P, ctypes.c_longlong, _P]),
     "fwr_get_status": (_I, [_P]),
+    "fwr_fp32_fma_peak": (_I, [_P, _P, _P]),
     "fwr_status_string": (ctypes.c_char_p, [_I]),
     "fwr_last_error": (ctypes.c_char_p, []),
 }
@@ -268,6 +272,32 @@ class Plan:
     def status(self):
         """Read and clear the sticky device status (synchronises)."""
         return STATUS.get(self._lib.fwr_get_status(self._h))
+
+
+def reconstruct_ragged(plans, frame_plan, slopes_ptrs, phase_ptrs, iters, stream=None):
+    """One-call ragged reconstruction (fwr_reconstruct_ragged): frame f through
+    plans[frame_plan[f]], one launch. frame_plan: int32 CUDA tensor (n_frames);
+    slopes_ptrs / phase_ptrs: int64 CUDA tensors of per-frame device pointers
+    (Batch.pointer_table). The schedule is built on the first call for these
+    arguments and kept until ragged_release()."""
+    import torch
+    lib = load()
+    if not (isinstance(frame_plan, torch.Tensor) and frame_plan.is_cuda and frame_plan.dtype == torch.int32
+            and frame_plan.is_contiguous() and frame_plan.dim() == 1):
+        raise ValueError("frame_plan must be a contiguous 1-D int32 CUDA tensor")
+    F = frame_plan.shape[0]
+    for t, name in ((slopes_ptrs, "slopes_ptrs"), (phase_ptrs, "phase_ptrs")):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.int64 and tuple(t.shape) == (F,)):
+            raise ValueError("%s must be an int64 CUDA tensor of %d pointers" % (name, F))
+    arr = (ctypes.c_void_p * len(plans))(*[p._h.value for p in plans])
+    _check(lib.fwr_reconstruct_ragged(ctypes.cast(arr, ctypes.c_void_p), len(plans), _ptr(frame_plan),
+                                      _ptr(slopes_ptrs), F, int(iters), _ptr(phase_ptrs), _stream(stream)),
+           "fwr_reconstruct_ragged")
+
+
+def ragged_release():
+    """Free the schedules kept by reconstruct_ragged (fwr_ragged_release)."""
+    load().fwr_ragged_release()
 
 
 class Batch:
@@ -493,9 +523,20 @@ class LinearWarmStart:
             pass
 
 
-def gemm_bf16_tc(A, B, out=None, stream=None):
+def fp32_fma_peak(stream=None):
+    """Measured FP32 FMA throughput of the current device (fwr_fp32_fma_peak):
+    (TFLOP/s, ms per timed launch)."""
+    lib = load()
+    t = ctypes.c_double()
+    ms = ctypes.c_double()
+    _check(lib.fwr_fp32_fma_peak(ctypes.byref(t), ctypes.byref(ms), _stream(stream)), "fwr_fp32_fma_peak")
+    return t.value, ms.value
+
+
+def gemm_bf16_tc(A, B, out=None, stream=None, wait_cycles=None):
     """D = A B^T (fwr_gemm_bf16_tc): A (M, K), B (N, K) bfloat16 CUDA tensors,
-    K a multiple of 8, N of 128; D float32 (M, N)."""
+    K a multiple of 8, N of 128; D float32 (M, N). wait_cycles: bound of the
+    issuer's and epilogue's waits (fwr_gemm_bf16_tc_limit; for timeout tests)."""
     import torch
     if A.dtype != torch.bfloat16 or B.dtype != torch.bfloat16 or A.dim() != 2 or B.dim() != 2:
         raise ValueError("A and B must be 2-D bfloat16 tensors")
@@ -509,8 +550,12 @@ def gemm_bf16_tc(A, B, out=None, stream=None):
         out = torch.empty((M, N), dtype=torch.float32, device=A.device)
     _need(out, torch.float32, (M, N), "out")
     lib = load()
-    _check(lib.fwr_gemm_bf16_tc(_ptr(A), _ptr(B), int(M), int(N), int(K), _ptr(out), _stream(stream)),
-           "fwr_gemm_bf16_tc")
+    if wait_cycles is None:
+        _check(lib.fwr_gemm_bf16_tc(_ptr(A), _ptr(B), int(M), int(N), int(K), _ptr(out), _stream(stream)),
+               "fwr_gemm_bf16_tc")
+    else:
+        _check(lib.fwr_gemm_bf16_tc_limit(_ptr(A), _ptr(B), int(M), int(N), int(K), _ptr(out), int(wait_cycles),
+                                          _stream(stream)), "fwr_gemm_bf16_tc_limit")
     return out
 
 

@@ -19,14 +19,9 @@ taken from the library), or of the extension itself (fit). The phase fit
 needs a far smaller rank: the pupil phase after one iteration depends on the
 warm start through a few hundred modes. The fit is off-line host work in FP64
 (numpy); inference runs entirely in the library (fwr_linws_reconstruct).
-
-    python -m paper_1705_04298_gb300.linws eval --rank 256
-    python -m paper_1705_04298_gb300.linws time --rank 256 --reps 20
+bench.py measures it against the plain loop.
 """
 
-import argparse
-import json
-import sys
 import time
 
 import numpy as np
@@ -166,106 +161,3 @@ def build(fwr, plan, mask, rank=DEFAULT_RANK, max_batch=1000, frames=TRAIN_FRAME
     if log:
         log("operator %.1f s, training slopes %.1f s, fit %.1f s" % (t1 - t0, t2 - t1, t3 - t2))
     return fwr.LinearWarmStart(plan, A, V, max_batch), E
-
-
-def evaluate(fwr, rank=DEFAULT_RANK, n_frames=1000, reps=20, log=print):
-    """Residual and frames/s of the plain loop against the linear warm start
-    followed by k = 1, 2 iterations, on the evaluation frames of the learned
-    warm start (40 x 40 lenslets, 128^2 grid, 0.05 rad noise, Wiener)."""
-    import torch
-    from . import synth
-    mask = synth.pupil_mask(learned.N_LENSLETS)
-    plan = learned.make_plan(fwr, fwr.WIENER, learned.EVAL_SIGMA)
-    ws, _ = build(fwr, plan, mask, rank, max_batch=n_frames, log=log)
-    slopes, truth = learned.frames(n_frames, learned.EVAL_SEED0, learned.EVAL_SIGMA)
-    phase = torch.empty((n_frames, learned.GRID, learned.GRID), device="cuda")
-    warm = torch.empty((n_frames, 2, learned.GRID, learned.GRID), device="cuda")
-
-    def timed(fn):
-        for _ in range(3):
-            fn()
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(reps):
-            fn()
-        e1.record()
-        torch.cuda.synchronize()
-        return e0.elapsed_time(e1) / reps
-
-    out = {}
-    for k in learned.PLAIN_ITERS:
-        ms = timed(lambda: plan.reconstruct(slopes, k, phase))
-        out["plain_k%d" % k] = {"residual_rad": learned.residual_rms(fwr, phase, truth, mask), "ms": ms,
-                                "frames_per_s": n_frames / ms * 1e3}
-    ms_ws = timed(lambda: ws.forward(slopes, warm))
-    ws.status()
-    for k in (1, 2):
-        def run():
-            ws.forward(slopes, warm)
-            plan.reconstruct(slopes, k, phase, ext_init=warm)
-        ms = timed(run)
-        r = learned.residual_rms(fwr, phase, truth, mask)
-        p10 = out["plain_k10"]
-        out["linear_r%d_k%d" % (rank, k)] = {
-            "residual_rad": r, "ms": ms, "warm_start_ms": ms_ws, "frames_per_s": n_frames / ms * 1e3,
-            "residual_vs_plain_k10": r / p10["residual_rad"], "speedup_vs_plain_k10": p10["ms"] / ms}
-    ws.status()
-    for key, v in out.items():
-        log("%-16s residual %.4f rad  %.3f ms  %.0f frames/s" % (key, v["residual_rad"], v["ms"],
-                                                                  v["frames_per_s"]))
-    return out
-
-
-def time_warm_start(fwr, rank=DEFAULT_RANK, n_frames=1000, reps=20, iters=1, log=print):
-    """Device time (CUDA events, mean of reps) of the warm start alone
-    (fwr_linws_forward: gather and the two tcgen05 GEMMs) and of the whole
-    fwr_linws_reconstruct call, on the evaluation frames."""
-    import torch
-    from . import synth
-    mask = synth.pupil_mask(learned.N_LENSLETS)
-    plan = learned.make_plan(fwr, fwr.WIENER, learned.EVAL_SIGMA)
-    ws, _ = build(fwr, plan, mask, rank, max_batch=n_frames, frames=1024)
-    slopes, _ = learned.frames(n_frames, learned.EVAL_SEED0, learned.EVAL_SIGMA)
-    warm = torch.empty((n_frames, 2, learned.GRID, learned.GRID), device="cuda")
-    phase = torch.empty((n_frames, learned.GRID, learned.GRID), device="cuda")
-    out = {}
-    for name, fn in (("warm_start", lambda: ws.forward(slopes, warm)),
-                     ("reconstruct_k%d" % iters, lambda: ws.reconstruct(slopes, iters, phase))):
-        for _ in range(3):
-            fn()
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(reps):
-            fn()
-        e1.record()
-        torch.cuda.synchronize()
-        out[name + "_ms"] = e0.elapsed_time(e1) / reps
-    ws.status()
-    log(json.dumps(out))
-    return out
-
-
-def main(argv=None):
-    ap = argparse.ArgumentParser()
-    ap.add_argument("cmd", choices=["eval", "time"])
-    ap.add_argument("--rank", type=int, default=DEFAULT_RANK)
-    ap.add_argument("--frames", type=int, default=1000)
-    ap.add_argument("--reps", type=int, default=20)
-    ap.add_argument("--iters", type=int, default=1)
-    args = ap.parse_args(argv)
-    from . import fwr
-    fwr.load()
-    if args.cmd == "time":
-        time_warm_start(fwr, args.rank, args.frames, args.reps, args.iters)
-        return 0
-    res = evaluate(fwr, args.rank, args.frames)
-    print(json.dumps(res))
-    return 0
-
-
-if __name__ == "__main__":
-    sys.exit(main())

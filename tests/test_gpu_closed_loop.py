@@ -44,3 +44,29 @@ def test_closed_loop_converges(fwr):
     assert tails["Gerchberg k = 1"] < 0.97 * tails["zero padding (k = 0)"]
     assert tails["Gerchberg k = 2, periodic"] < 0.97 * tails["zero padding (k = 0)"]
     assert tails["Hudgin (k = 0, periodic)"] > 1.1 * tails["Gerchberg k = 2, periodic"]
+
+
+@pytest.mark.parametrize("k,periodic", [(1, 2), (2, 0)])
+def test_closed_loop_trace_matches_oracle(fwr, k, periodic):
+    """Closed-loop parity: the same seeded loops (4 loops, 40x40 lenslets on
+    128^2, gain 0.5, one frame of delay, 0.02 rad noise, 20 frames) with the
+    library's FP32 path and with the FP64 oracle as the reconstructor. The
+    residual traces agree step by step within the FP32 bound; feedback does
+    not amplify the per-step differences (the loop is stable)."""
+    import oracle
+    from paper_1705_04298_gb300 import closed_loop
+    n, pad, steps = 40, 3.2, 20
+    data = closed_loop.turbulence(n=n, steps=steps, loops=4, seed0=300)
+    mask = data[2]
+    rec_gpu = closed_loop.library_reconstructor(fwr, mask, pad, k, periodic)
+
+    def rec_oracle(slopes):
+        return np.stack([oracle.reconstruct(s, mask, pad, k, periodic=periodic)[0] for s in slopes])
+
+    g = closed_loop.simulate(rec_gpu, gain=0.5, sigma=0.02, data=data)
+    o = closed_loop.simulate(rec_oracle, gain=0.5, sigma=0.02, data=data)
+    assert np.array_equal(g["open_loop"], o["open_loop"])
+    rel = np.abs(g["residual"] - o["residual"]) / o["residual"]
+    print("closed-loop trace k=%d periodic=%d: worst relative step difference %.2e" % (k, periodic, rel.max()))
+    assert rel.max() < 1e-5
+    assert o["residual"][-1] < 0.3 * o["open_loop"][-1]

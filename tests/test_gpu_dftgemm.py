@@ -13,9 +13,16 @@ import pytest
 
 import oracle
 from paper_1705_04298_gb300 import synth
+from parity_check import errors, within
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
+
+# Bounds of the split-BF16 reconstructions against the FP64 oracle: about three
+# times the worst error measured on a GB300 over these cases (rms 2.3e-5 at
+# 32^2, k = 10; element-wise: being measured).
+DFT_RMS = 7e-5
+DFT_MAX = 1e-3
 
 
 @pytest.fixture(scope="module")
@@ -28,10 +35,7 @@ def fwr():
 
 
 def rel_rms(got, ref):
-    d = np.asarray(got, np.float64) - ref
-    d -= d.mean()
-    r = ref - ref.mean()
-    return float(np.sqrt(np.sum(d * d) / np.sum(r * r)))
+    return errors(got, ref)[0]
 
 
 @pytest.mark.parametrize("N", [32, 64])
@@ -62,8 +66,8 @@ def test_reconstruction_with_tensor_core_dft(fwr, n, pad, k, filt):
                                     oracle.FILTER_WIENER if filt == "wiener" else oracle.FILTER_LSQ,
                                     sig ** 2, r0p, L0p)
         worst = max(worst, rel_rms(ph[f], ref))
+        assert within(ph[f], ref, DFT_RMS, DFT_MAX, where="N=%d k=%d f=%d" % (plan.N, k, f))
     print("split-BF16 DFT reconstruction n=%d N=%d k=%d: relative phase rms %.2e" % (n, plan.N, k, worst))
-    assert worst < 1e-3
 
 
 @pytest.mark.parametrize("n,pad,k,filt,periodic", [(40, 3.2, 10, "wiener", 0), (40, 3.2, 2, "lsq", 1),
@@ -88,9 +92,9 @@ def test_batched_tensor_core_dft_reconstruction(fwr, n, pad, k, filt, periodic):
                                     oracle.FILTER_WIENER if filt == "wiener" else oracle.FILTER_LSQ,
                                     sig ** 2, r0p, L0p, periodic)
         worst = max(worst, rel_rms(ph[f], ref))
+        assert within(ph[f], ref, DFT_RMS, DFT_MAX, where="N=%d k=%d periodic=%d f=%d" % (plan.N, k, periodic, f))
     print("batched split-BF16 DFT n=%d N=%d k=%d periodic=%d: relative phase rms %.2e"
           % (n, plan.N, k, periodic, worst))
-    assert worst < 1e-4
 
 
 def test_batched_tensor_core_dft_chunks_and_limits(fwr):

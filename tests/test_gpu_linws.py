@@ -52,6 +52,27 @@ def test_gemm_argument_errors(fwr):
         fwr.gemm_bf16_tc(A12, torch.zeros(128, 12, dtype=torch.bfloat16, device="cuda"))  # K % 8
 
 
+def test_gemm_wait_timeout_reports_and_recovers(fwr):
+    """The bounded-wait path of the tcgen05 GEMM: with a 16-cycle bound the MMA
+    issuer gives up before the first TMA tiles land; the kernel drains its
+    loads (full bound), frees its tensor memory and reports FWR_ERR_TIMEOUT.
+    The context stays usable: the same product then comes out right."""
+    g = torch.Generator().manual_seed(11)
+    A = torch.randn(256, 512, generator=g).bfloat16()
+    B = torch.randn(256, 512, generator=g).bfloat16()
+    Ad, Bd = A.cuda(), B.cuda()
+    with pytest.raises(fwr.FwrError) as e:
+        fwr.gemm_bf16_tc(Ad, Bd, wait_cycles=16)
+    assert e.value.code == 5
+    D = fwr.gemm_bf16_tc(Ad, Bd).double().cpu()
+    ref = A.double() @ B.double().T
+    scale = (A.double().abs() @ B.double().abs().T).max()
+    assert float((D - ref).abs().max()) <= 2e-6 * float(scale)
+    with pytest.raises(fwr.FwrError) as e:
+        fwr.gemm_bf16_tc(Ad, Bd, wait_cycles=0)
+    assert e.value.code == 1
+
+
 def small_setup(fwr):
     n, pad = 16, 2.0
     mask = synth.pupil_mask(n)

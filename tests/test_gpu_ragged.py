@@ -11,6 +11,7 @@ import pytest
 
 import oracle
 from paper_1705_04298_gb300 import synth
+from parity_check import within
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -26,13 +27,6 @@ def fwr():
     from paper_1705_04298_gb300 import fwr as m
     m.load()
     return m
-
-
-def rel_rms(got, ref):
-    d = np.asarray(got, np.float64) - ref
-    d -= d.mean()
-    r = ref - ref.mean()
-    return float(np.sqrt(np.sum(d * d) / np.sum(r * r)))
 
 
 def make_batch(fwr, per_size, k, seed=7):
@@ -65,7 +59,7 @@ def test_ragged_matches_per_plan_and_oracle(fwr):
         if pl not in checked:
             n, pad = SIZES[pl]
             orc, _ = oracle.reconstruct(host[f], synth.pupil_mask(n), pad, k, oracle.FILTER_LSQ)
-            assert rel_rms(phases[f].cpu().numpy(), orc) <= FP32_TOL
+            assert within(phases[f].cpu().numpy(), orc, FP32_TOL, where="N=%d" % plans[pl].N)
             checked.add(pl)
     assert len(checked) == len(SIZES)
 
@@ -131,3 +125,60 @@ def test_ragged_errors_and_status(fwr):
     p = [torch.empty((128, 128), device="cuda") for _ in range(2)]
     batch.run(fwr.Batch.pointer_table(s), fwr.Batch.pointer_table(p))
     assert big.status() == "FWR_ERR_NONFINITE"
+
+
+def test_reconstruct_ragged_one_call_against_oracle(fwr):
+    """fwr_reconstruct_ragged (device frame table, one launch): every frame
+    against the FP64 oracle, bitwise equal to the batch object's result and
+    to a second (cached, allocation-free) call and its CUDA-graph replay."""
+    k = 2
+    plans, batch, frame_plan, host, slopes, phases = make_batch(fwr, 2, k, seed=21)
+    sp, pp = fwr.Batch.pointer_table(slopes), fwr.Batch.pointer_table(phases)
+    fpd = torch.tensor(frame_plan, dtype=torch.int32, device="cuda")
+    fwr.reconstruct_ragged(plans, fpd, sp, pp, k)
+    torch.cuda.synchronize()
+    first = [p.clone() for p in phases]
+    for f, pl in enumerate(frame_plan):
+        n, pad = SIZES[pl]
+        orc, _ = oracle.reconstruct(host[f], synth.pupil_mask(n), pad, k, oracle.FILTER_LSQ)
+        assert within(first[f].cpu().numpy(), orc, FP32_TOL, where="frame %d N=%d" % (f, plans[pl].N))
+    batch.run(sp, pp)
+    torch.cuda.synchronize()
+    for a, b in zip(phases, first):
+        assert torch.equal(a, b)
+    for p in phases:
+        p.zero_()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        fwr.reconstruct_ragged(plans, fpd, sp, pp, k, stream=s)
+    g.replay()
+    torch.cuda.synchronize()
+    for a, b in zip(phases, first):
+        assert torch.equal(a, b)
+    fwr.ragged_release()
+
+
+def test_reconstruct_ragged_rejects_bad_tables(fwr):
+    big = fwr.Plan(synth.pupil_mask(40), 3.2, fwr.LSQ)
+    fr = synth.frame(40, 1, 0.05)["slopes"]
+    s = [torch.tensor(fr, dtype=torch.float32, device="cuda") for _ in range(2)]
+    p = [torch.empty((128, 128), device="cuda") for _ in range(2)]
+    sp, pp = fwr.Batch.pointer_table(s), fwr.Batch.pointer_table(p)
+    with pytest.raises(fwr.FwrError) as e:
+        fwr.reconstruct_ragged([big], torch.tensor([0, 1], dtype=torch.int32, device="cuda"), sp, pp, 1)
+    assert e.value.code == 1
+    # a table rewritten in place after the first call: the bad frame is skipped and reported
+    fpd = torch.tensor([0, 0], dtype=torch.int32, device="cuda")
+    fwr.reconstruct_ragged([big], fpd, sp, pp, 1)
+    torch.cuda.synchronize()
+    good = p[0].clone()
+    p[0].zero_()
+    fpd[1] = 5
+    fwr.reconstruct_ragged([big], fpd, sp, pp, 1)
+    torch.cuda.synchronize()
+    assert torch.equal(p[0], good)
+    assert big.status() == "FWR_ERR_ARG"
+    assert big.status() == "FWR_OK"
+    fwr.ragged_release()

@@ -1,4 +1,4 @@
-"""Pins of the oracle's Hudgin extension (Sec. 3.1): the closed form for a tilt
+"""Pins of the oracle's Hudgin extension (Sec. 3.2): the closed form for a tilt
 and its place in the full path (the hand-worked example is the fixture
 tests/golden/hudgin_6x6.txt, checked in tests/test_golden.py)."""
 
