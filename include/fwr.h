@@ -155,6 +155,21 @@ fwr_status fwr_plan_create(fwr_plan** out, int n_lenslets, double pad_factor,
                            const uint8_t* pupil_mask, int filter, double noise_var,
                            double r0, double L0);
 
+/*
+ * As fwr_plan_create, with the grid size N given instead of a pad factor:
+ * the paper's small windows of w lenslets around the pupil (N = n + 2w,
+ * Sec. 4.1: w = 3 and 6). N >= n + 2. A power of two in {16, ..., 256} gives
+ * the same plan as fwr_plan_create. Any other N must be even and in
+ * [16, 64]: such plans run the direct-DFT kernel (every 1-D transform a
+ * direct sum over the line, O(N) per output) in FP32 and FP64 through
+ * fwr_reconstruct, _ex, _f64 and _host, with every periodic mode, both
+ * filters, warm starts and ext_out; the Hudgin extension, the DFT-as-GEMM
+ * transform, ragged batches, the static-scratch call and warm-start objects
+ * return FWR_ERR_UNSUPPORTED for them. FWR_ERR_UNSUPPORTED for other N.
+ */
+fwr_status fwr_plan_create_grid(fwr_plan** out, int n_lenslets, int N, const uint8_t* pupil_mask, int filter,
+                                double noise_var, double r0, double L0);
+
 /* Free a plan and its device tables (NULL is ignored). Not stream-ordered:
  * the caller makes sure no work using the plan is still running. */
 void fwr_plan_destroy(fwr_plan* plan);
@@ -201,7 +216,7 @@ fwr_status fwr_reconstruct_ex(fwr_plan* plan, const float* slopes_dev, const flo
                               void* stream);
 
 /*
- * The same computation in FP64 throughout (tables, FFTs, filters). Same
+ * The same computation in FP64 throughout (tables, transforms, filters). Same
  * layouts with double elements. Supported for N <= 64 (an FP64 grid of
  * 128^2 does not fit in one SM's shared memory): FWR_ERR_UNSUPPORTED
  * otherwise. Meant for parity checks, not throughput.

@@ -324,17 +324,21 @@ def final_reconstruct(sx, sy, Rx, Ry):
 
 def reconstruct(slopes, mask, pad_factor, iters, filt=FILTER_LSQ, noise_var=0.0,
                 r0_pitch=1.0, L0_pitch=1.0, periodic=PERIODIC_BEFORE_EACH_FFT,
-                ext_init=None, history=None, g_model=G_AVERAGED, pixel=0.0):
+                ext_init=None, history=None, g_model=G_AVERAGED, pixel=0.0, N=None):
     """Whole path for one frame: embed -> Gerchberg extension -> final filter.
 
     slopes: (2, n, n) x then y slopes in radians per lenslet; mask: (n, n).
     g_model, pixel: the measurement model (G_AVERAGED or G_FRIED; d_px / d).
+    N: the grid size itself (any N >= n + 2; the paper's windows of w
+    lenslets around the pupil are N = n + 2w, Sec. 4.1) instead of the power
+    of two that pad_factor gives.
     Returns (phase N x N, extended slopes (2, N, N)).
     """
     slopes = np.asarray(slopes, dtype=np.float64)
     mask = np.asarray(mask).astype(bool)
     n = mask.shape[0]
-    N = grid_size(n, pad_factor)
+    if N is None:
+        N = grid_size(n, pad_factor)
     s0x, s0y, P = embed(slopes, mask, N)
     sx, sy = gerchberg_extend(s0x, s0y, P, iters, periodic, ext_init, history, g_model, pixel)
     Rx, Ry = reconstruction_filters(N, filt, noise_var, r0_pitch, L0_pitch, g_model, pixel)

@@ -188,6 +188,21 @@ fwr::Tables<T> view(const fwr::DevTables<T>& d) {
 
 bool supported_grid(int N) { return N == 16 || N == 32 || N == 64 || N == 128 || N == 256; }
 
+
+bool pow2(int N) { return N > 0 && (N & (N - 1)) == 0; }
+
+fwr_status check_common(int n, const uint8_t* pupil_mask, int filter, double noise_var, double r0, double L0) {
+    if (n < 2 || !pupil_mask) return FWR_ERR_ARG;
+    if (filter != FWR_LSQ && filter != FWR_WIENER) return FWR_ERR_ARG;
+    if (!(noise_var >= 0.0) || !std::isfinite(noise_var)) return FWR_ERR_ARG;
+    if (filter == FWR_WIENER && (!(r0 > 0.0) || !(L0 > 0.0) || !std::isfinite(r0) || !std::isfinite(L0)))
+        return FWR_ERR_ARG;
+    return FWR_OK;
+}
+
+fwr_status plan_create_n(fwr_plan** out, int n, int N, const uint8_t* pupil_mask, int filter, double noise_var,
+                         double r0, double L0);
+
 }  // namespace
 
 extern "C" {
@@ -196,16 +211,34 @@ fwr_status fwr_plan_create(fwr_plan** out, int n, double pad_factor, const uint8
                            double noise_var, double r0, double L0) {
     if (!out) return FWR_ERR_ARG;
     *out = nullptr;
-    if (n < 2 || !pupil_mask || !(pad_factor >= 1.0) || !std::isfinite(pad_factor)) return FWR_ERR_ARG;
-    if (filter != FWR_LSQ && filter != FWR_WIENER) return FWR_ERR_ARG;
-    if (!(noise_var >= 0.0) || !std::isfinite(noise_var)) return FWR_ERR_ARG;
-    if (filter == FWR_WIENER && (!(r0 > 0.0) || !(L0 > 0.0) || !std::isfinite(r0) || !std::isfinite(L0)))
-        return FWR_ERR_ARG;
+    if (!(pad_factor >= 1.0) || !std::isfinite(pad_factor)) return FWR_ERR_ARG;
+    fwr_status st = check_common(n, pupil_mask, filter, noise_var, r0, L0);
+    if (st != FWR_OK) return st;
     const double want = std::ceil(pad_factor * n - 1e-9);
     if (want > 4096.0) return FWR_ERR_UNSUPPORTED;
     const int N = next_pow2(int(want));
     if (N < n + 2) return FWR_ERR_ARG;
     if (!supported_grid(N)) return FWR_ERR_UNSUPPORTED;
+    return plan_create_n(out, n, N, pupil_mask, filter, noise_var, r0, L0);
+}
+
+fwr_status fwr_plan_create_grid(fwr_plan** out, int n, int N, const uint8_t* pupil_mask, int filter,
+                                double noise_var, double r0, double L0) {
+    if (!out) return FWR_ERR_ARG;
+    *out = nullptr;
+    fwr_status st = check_common(n, pupil_mask, filter, noise_var, r0, L0);
+    if (st != FWR_OK) return st;
+    if (N < n + 2) return FWR_ERR_ARG;
+    if (pow2(N) ? !supported_grid(N) : (N % 2 != 0 || N < 16 || N > 64)) return FWR_ERR_UNSUPPORTED;
+    return plan_create_n(out, n, N, pupil_mask, filter, noise_var, r0, L0);
+}
+
+}  // extern "C"
+
+namespace {
+
+fwr_status plan_create_n(fwr_plan** out, int n, int N, const uint8_t* pupil_mask, int filter, double noise_var,
+                         double r0, double L0) {
     int nvalid = 0;
     for (int i = 0; i < n * n; ++i) nvalid += pupil_mask[i] ? 1 : 0;
     if (nvalid == 0) return FWR_ERR_ARG;
@@ -277,6 +310,10 @@ fwr_status fwr_plan_create(fwr_plan** out, int n, double pad_factor, const uint8
     *out = p;
     return FWR_OK;
 }
+
+}  // namespace
+
+extern "C" {
 
 void fwr_plan_destroy(fwr_plan* p) {
     if (!p) return;
@@ -359,7 +396,7 @@ fwr_status fwr_plan_set_option(fwr_plan* p, int key, double value) {
         const int v = int(value);
         if (double(v) != value || (v != FWR_TRANSFORM_FFT && v != FWR_TRANSFORM_DFT_BF16X3)) return FWR_ERR_ARG;
         if (v == FWR_TRANSFORM_DFT_BF16X3 && p->N != 32 && p->N != 64 && p->N != 128 && p->N != 256)
-            return FWR_ERR_UNSUPPORTED;
+            return FWR_ERR_UNSUPPORTED;  // (non-power-of-two grids included)
         if (v == FWR_TRANSFORM_DFT_BF16X3 && p->N >= 128 && !p->d_dftws) {
             // batched tensor-core path: its workspace is made here, not in the reconstruct calls
             int prev = 0;
@@ -426,12 +463,15 @@ fwr_status fwr_reconstruct_ex(fwr_plan* p, const float* slopes, const float* ext
     k.status = p->d_status;
     const bool hudgin = p->extension == FWR_EXT_HUDGIN && !ext_init;
     if (hudgin) {
-        if (p->transform == FWR_TRANSFORM_DFT_BF16X3 || (p->N != 256 && !fwr::fused_supported(p->N, 4, p->n)))
+        if (p->transform == FWR_TRANSFORM_DFT_BF16X3 || !pow2(p->N) ||
+            (p->N != 256 && !fwr::fused_supported(p->N, 4, p->n)))
             return FWR_ERR_UNSUPPORTED;
         k.hud = p->d_hud;
     }
     cudaError_t e;
-    if (p->transform == FWR_TRANSFORM_DFT_BF16X3) {
+    if (!pow2(p->N)) {
+        e = fwr::launch_anygrid_f32(p->N, k, static_cast<cudaStream_t>(stream));
+    } else if (p->transform == FWR_TRANSFORM_DFT_BF16X3) {
         if (p->N >= 128) {
             if (ext_out || !phase) return FWR_ERR_UNSUPPORTED;
             e = fwr::launch_dftgemm_f32(p->N, k, p->d_dftws, static_cast<cudaStream_t>(stream));
@@ -523,10 +563,11 @@ fwr_status fwr_reconstruct_f64(fwr_plan* p, const double* slopes, const double* 
     k.periodic = p->periodic;
     k.status = p->d_status;
     if (p->extension == FWR_EXT_HUDGIN && !ext_init) {
-        if (!fwr::fused_supported(p->N, 8, p->n)) return FWR_ERR_UNSUPPORTED;
+        if (!pow2(p->N) || !fwr::fused_supported(p->N, 8, p->n)) return FWR_ERR_UNSUPPORTED;
         k.hud = p->d_hud;
     }
-    cudaError_t e = fwr::fused_supported(p->N, 8, p->n)
+    cudaError_t e = !pow2(p->N) ? fwr::launch_anygrid_f64(p->N, k, static_cast<cudaStream_t>(stream))
+                    : fwr::fused_supported(p->N, 8, p->n)
                         ? fwr::launch_fused_f64(p->N, k, static_cast<cudaStream_t>(stream))
                         : fwr::launch_basic_f64(p->N, k, static_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? FWR_OK : cuda_fail(e, "gerchberg f64 launch");

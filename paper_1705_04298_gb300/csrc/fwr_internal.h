@@ -100,6 +100,12 @@ size_t ragged_smem_bytes(int N, int n);  // 0 if the plan cannot join a ragged b
 cudaError_t ragged_prepare(size_t smem);
 cudaError_t launch_ragged(const RaggedParams& p, int grid, size_t smem, cudaStream_t s);
 
+// Grids of any even size 16 <= N <= 64 (fwr_anygrid.cu): direct-DFT kernel
+// for the paper's small windows around the pupil.
+size_t anygrid_smem_bytes(int N, int elem_bytes, int n);
+cudaError_t launch_anygrid_f32(int N, const Params<float>& p, cudaStream_t s);
+cudaError_t launch_anygrid_f64(int N, const Params<double>& p, cudaStream_t s);
+
 // Main fused kernel (fwr_fused.cu). fused_supported() says whether its
 // shared-memory layout fits grid N with n lenslets for the element size.
 bool fused_supported(int N, int elem_bytes, int n);

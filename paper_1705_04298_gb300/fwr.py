@@ -45,6 +45,7 @@ _I = ctypes.c_int
 _D = ctypes.c_double
 SIGNATURES = {
     "fwr_plan_create": (_I, [ctypes.POINTER(_P), _I, _D, _P, _I, _D, _D, _D]),
+    "fwr_plan_create_grid": (_I, [ctypes.POINTER(_P), _I, _I, _P, _I, _D, _D, _D]),
     "fwr_plan_destroy": (None, [_P]),
     "fwr_plan_grid": (_I, [_P]),
     "fwr_plan_valid_count": (_I, [_P]),
@@ -149,11 +150,13 @@ def _need(t, dtype, shape, name):
 class Plan:
     """A reconstruction plan (fwr_plan_create): pupil, grid, filters.
 
-    mask: (n, n) array-like of bool; r0 and L0 in lenslet pitches.
+    mask: (n, n) array-like of bool; r0 and L0 in lenslet pitches. grid: the
+    grid size N itself (fwr_plan_create_grid: any even N in [16, 64] or a
+    power of two up to 256) instead of the next power of two >= pad_factor n.
     """
 
     def __init__(self, mask, pad_factor=2.0, filter=LSQ, noise_var=0.0, r0=1.0, L0=100.0,
-                 periodic=PERIODIC_BEFORE_EACH_FFT):
+                 periodic=PERIODIC_BEFORE_EACH_FFT, grid=None):
         lib = load()
         m = np.ascontiguousarray(np.asarray(mask).astype(np.uint8))
         if m.ndim != 2 or m.shape[0] != m.shape[1]:
@@ -161,9 +164,14 @@ class Plan:
         self.n = m.shape[0]
         self._lib = lib
         h = ctypes.c_void_p()
-        _check(lib.fwr_plan_create(ctypes.byref(h), self.n, float(pad_factor),
-                                   m.ctypes.data_as(ctypes.c_void_p), int(filter),
-                                   float(noise_var), float(r0), float(L0)), "fwr_plan_create")
+        if grid is None:
+            _check(lib.fwr_plan_create(ctypes.byref(h), self.n, float(pad_factor),
+                                       m.ctypes.data_as(ctypes.c_void_p), int(filter),
+                                       float(noise_var), float(r0), float(L0)), "fwr_plan_create")
+        else:
+            _check(lib.fwr_plan_create_grid(ctypes.byref(h), self.n, int(grid),
+                                            m.ctypes.data_as(ctypes.c_void_p), int(filter),
+                                            float(noise_var), float(r0), float(L0)), "fwr_plan_create_grid")
         self._h = h
         self.N = lib.fwr_plan_grid(h)
         self.valid_count = lib.fwr_plan_valid_count(h)

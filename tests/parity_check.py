@@ -25,9 +25,11 @@ import numpy as np
 
 FP32_RMS = 1e-5
 FP64_RMS = 1e-11
-# measured worst max/max ratio over the suite: (being measured)
-FP32_MAX = 1e-4
-FP64_MAX = 1e-10
+# measured worst element-wise ratio over the suite on a GB300: FP32 paths
+# 1.24e-6 (40x40 on 128^2, k = 10, Wiener, frame 999 of the 1000-frame
+# launch), FP64 path 1.48e-14 (Hudgin extension, 64^2)
+FP32_MAX = 4e-6
+FP64_MAX = 5e-14
 
 
 def errors(got, ref):

@@ -19,10 +19,10 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 # Bounds of the split-BF16 reconstructions against the FP64 oracle: about three
-# times the worst error measured on a GB300 over these cases (rms 2.3e-5 at
-# 32^2, k = 10; element-wise: being measured).
+# times the worst error measured on a GB300 over these cases (rms 2.27e-5 and
+# element-wise 3.0e-5, both at 32^2, k = 10).
 DFT_RMS = 7e-5
-DFT_MAX = 1e-3
+DFT_MAX = 1e-4
 
 
 @pytest.fixture(scope="module")

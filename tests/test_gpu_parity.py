@@ -438,3 +438,58 @@ def test_hudgin_extension_unsupported_paths(fwr):
         plan.reconstruct(torch.tensor(sl, dtype=torch.float32, device="cuda"), 1)
     with pytest.raises(fwr.FwrError):
         plan.set_extension(2)
+
+
+# --------------------------- non-power-of-two windows (direct-DFT kernel) --
+
+@pytest.mark.parametrize("N,k,periodic,filt", [(46, 10, 0, "wiener"), (52, 10, 0, "wiener"), (46, 2, 1, "lsq"),
+                                               (52, 3, 2, "lsq"), (42, 1, 0, "lsq")])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_window_grids_against_oracle(fwr, N, k, periodic, filt, precision):
+    """40 lenslets on the paper's small windows (N = n + 2w, w = 3 and 6, Sec.
+    4.1; and w = 1) through fwr_plan_create_grid: FP32 and FP64 against the
+    FP64 oracle on the same grid, with the extended slopes' in-pupil cells
+    bitwise equal to the measurement."""
+    n, sigma = 40, 0.05
+    r0p, L0p = synth.pitch_units(n, 0.15, 25.0)
+    F = 3
+    sl, _, mask = synth.batch(n, F, 4600 + N + k, sigma)
+    fl = fwr.WIENER if filt == "wiener" else fwr.LSQ
+    plan = fwr.Plan(mask, 1.0, fl, sigma ** 2, r0p, L0p, periodic, grid=N)
+    assert plan.N == N
+    dtype = torch.float64 if precision == "fp64" else torch.float32
+    tol = FP64_TOL if precision == "fp64" else FP32_TOL
+    s = torch.tensor(sl, dtype=dtype, device="cuda")
+    ext = torch.empty((F, 2, N, N), dtype=dtype, device="cuda")
+    ph = (plan.reconstruct_f64 if precision == "fp64" else plan.reconstruct)(s, k, ext_out=ext).cpu().numpy()
+    eo = ext.cpu().numpy().astype(np.float64)
+    for f in range(F):
+        ref, ref_ext = oracle.reconstruct(sl[f], mask, 1.0, k, FILTERS[filt], sigma ** 2, r0p, L0p, periodic, N=N)
+        assert within(ph[f], ref, tol, where="N=%d f=%d" % (N, f))
+        assert within(eo[f], ref_ext, 10 * tol, 10 * max_tol_for(tol), where="N=%d ext f=%d" % (N, f))
+        s0x, s0y, P = oracle.embed(sl[f], mask, N)
+        dt = np.float64 if precision == "fp64" else np.float32
+        assert np.array_equal(eo[f][0][P].astype(dt), s0x[P].astype(dt))
+        assert np.array_equal(eo[f][1][P].astype(dt), s0y[P].astype(dt))
+    assert plan.status() == "FWR_OK"
+
+
+def test_window_grid_options_and_limits(fwr):
+    mask = synth.pupil_mask(40)
+    plan = fwr.Plan(mask, 1.0, fwr.LSQ, grid=46)
+    with pytest.raises(fwr.FwrError) as e:
+        plan.set_transform(fwr.TRANSFORM_DFT_BF16X3)
+    assert e.value.code == 2
+    plan.set_extension(fwr.EXT_HUDGIN)
+    with pytest.raises(fwr.FwrError) as e:
+        plan.reconstruct(torch.zeros((1, 2, 40, 40), device="cuda"), 1)
+    assert e.value.code == 2
+    for bad, code in ((47, 2), (66, 2), (41, 1)):
+        with pytest.raises(fwr.FwrError) as e:
+            fwr.Plan(mask, 1.0, fwr.LSQ, grid=bad)
+        assert e.value.code == code
+    # a power of two through the explicit-grid call is the regular plan
+    p128 = fwr.Plan(mask, 1.0, fwr.LSQ, grid=128)
+    ref = fwr.Plan(mask, 3.2, fwr.LSQ)
+    s = torch.tensor(synth.batch(40, 2, 5, 0.05)[0], dtype=torch.float32, device="cuda")
+    assert torch.equal(p128.reconstruct(s, 2), ref.reconstruct(s, 2))

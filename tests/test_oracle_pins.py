@@ -35,7 +35,7 @@ def _rng(seed):
 
 # ---------------------------------------------------------------- P1 -------
 
-@pytest.mark.parametrize("N", [4, 8])
+@pytest.mark.parametrize("N", [4, 8, 6, 10])  # 6, 10: non-power-of-two grids (the paper's windows)
 def test_p1_dft_matches_bruteforce(N):
     rng = _rng(N)
     x = rng.standard_normal((N, N)) + 1j * rng.standard_normal((N, N))
@@ -97,7 +97,7 @@ def _exact_mode_slopes(N, u, v, A=1.0 + 0.0j, nodes=24):
     return sx, sy, phi(n, m)
 
 
-@pytest.mark.parametrize("N", [8, 16])
+@pytest.mark.parametrize("N", [8, 16, 10])
 def test_p2_filters_match_exact_lenslet_average(N):
     Gx, Gy = oracle.measurement_filters(N)
     u_of = oracle.signed_freq(N)
@@ -196,6 +196,27 @@ def test_p3_single_mode_fixed_point(mode):
     hist = []
     phase, ext = oracle.reconstruct(slopes, mask, 2.0, 4, oracle.FILTER_LSQ, periodic=mode,
                                     ext_init=np.stack([sx, sy]), history=hist)
+    for hx, hy in hist:
+        assert np.max(np.abs(hx - sx)) <= 1e-12 and np.max(np.abs(hy - sy)) <= 1e-12
+    assert np.max(np.abs(phase - (phi - phi.mean()))) <= 1e-12
+
+
+@pytest.mark.parametrize("mode", [oracle.PERIODIC_BEFORE_EACH_FFT, oracle.PERIODIC_NONE])
+def test_p3_single_mode_fixed_point_on_a_window_grid(mode):
+    """The same fixed point on a non-power-of-two grid: 40 lenslets with a
+    window of 3 lenslets on each side (N = 46, Sec. 4.1)."""
+    N, n = 46, 40
+    u, v = 5 / N, -7 / N
+    sx, sy, phi = _mode_problem(N, n, u, v, 0.3 + 0.9j)
+    mask = synth.pupil_mask(n)
+    off = oracle.pupil_offset(n, N)
+    assert off == 3
+    slopes = np.stack([sx[off:off + n, off:off + n], sy[off:off + n, off:off + n]])
+    slopes = np.where(mask[None], slopes, 0.0)
+    hist = []
+    phase, ext = oracle.reconstruct(slopes, mask, 1.0, 3, oracle.FILTER_LSQ, periodic=mode,
+                                    ext_init=np.stack([sx, sy]), history=hist, N=N)
+    assert phase.shape == (N, N)
     for hx, hy in hist:
         assert np.max(np.abs(hx - sx)) <= 1e-12 and np.max(np.abs(hy - sy)) <= 1e-12
     assert np.max(np.abs(phase - (phi - phi.mean()))) <= 1e-12
