@@ -308,19 +308,35 @@ def extra_measurements(fwr, synth, torch, flush):
     g.replay()
     ms = _time_launches(g.replay, flush, 10, torch)
     fl = sum(flops_per_frame(plans[pl].N, 5) for pl in fp)
+    # each size class alone (its 1024 frames through the same kernel, one launch)
+    per_class = {}
+    for pl, (n, _) in enumerate(sizes):
+        idx = [i for i, q in enumerate(fp) if q == pl]
+        spc = fwr.Batch.pointer_table([slopes[i] for i in idx])
+        ppc = fwr.Batch.pointer_table([phases[i] for i in idx])
+        bc = fwr.Batch(plans, [pl] * len(idx), 5)
+        bc.set_shape(batch.shape)
+        bc.run(spc, ppc)
+        msc = _time_launches(lambda: bc.run(spc, ppc), flush, 5, torch)
+        flc = flops_per_frame(plans[pl].N, 5) * len(idx)
+        per_class["%dx%d_on_%d" % (n, n, plans[pl].N)] = {
+            "frames": len(idx), "ms": msc, "frames_per_s": len(idx) / (msc / 1e3),
+            "frac": flc / (msc / 1e3) / 1e12 / peak}
     res["ragged_4096_40-64-80-128_k5"] = {"frames_per_s": 4096 / (ms / 1e3), "ms": ms,
                                           "tflops": fl / (ms / 1e3) / 1e12, "frac": fl / (ms / 1e3) / 1e12 / peak,
-                                          "launches": 1, "graph": True, "ctas": ctas, "cost_ratio": ratio}
+                                          "launches": 1, "graph": True, "ctas": ctas, "cost_ratio": ratio,
+                                          "shape": batch.shape, "size_classes_alone": per_class}
     # 128x128 lenslets on 256^2, k = 10, frozen-flow frames
     sl4, _, m4 = synth.frozen_flow(128, 32, 7, 0.05, r0=0.12, L0=25.0)
     p4 = fwr.Plan(m4, 2.0, fwr.LSQ)
     s4 = torch.tensor(sl4, dtype=torch.float32, device="cuda").repeat(32, 1, 1, 1)[:1000].contiguous()
     ph4 = torch.empty((1000, 256, 256), device="cuda")
+    launch4 = p4.autotune(s4, 10, ph4, os.path.join(OUT_DIR, "fwr_plan_tune.jsonl"))
     p4.reconstruct(s4, 10, ph4)
     ms = _time_launches(lambda: p4.reconstruct(s4, 10, ph4), flush, 5, torch)
     tf = flops_per_frame(256, 10) * 1000 / (ms / 1e3) / 1e12
     res["128x128_256grid_k10_frozen_flow"] = {"frames_per_s": 1000 / (ms / 1e3), "ms": ms, "tflops": tf,
-                                              "frac": tf / peak}
+                                              "frac": tf / peak, "launch": {"shape": launch4[0], "ctas": launch4[1]}}
     # the same frames through the split-BF16 DFT-as-GEMM transform (batched
     # tcgen05 GEMMs): 2 GEMMs per 2-D transform, 2 (k + 1) transforms, each
     # GEMM 2 x (2N) x (6N) x N flop per frame
@@ -616,6 +632,9 @@ def main():
         if dist is not None:
             dist.barrier()
 
+    # launch shape picked by timing on this workload (cached per device, driver, problem)
+    os.makedirs(OUT_DIR, exist_ok=True)
+    launch = plan.autotune(slopes, k, phase, os.path.join(OUT_DIR, "fwr_plan_tune.jsonl"))
     for _ in range(args.warmup):
         plan.reconstruct(slopes, k, phase)
     torch.cuda.synchronize()
@@ -680,7 +699,8 @@ def main():
                                    "per GPU, k=%d Gerchberg iterations, Wiener sigma=%g rad" % (FRAMES, k, SIGMA),
                        "n_lenslets": N_LENSLETS, "grid": N, "frames_per_gpu": FRAMES, "iters": k,
                        "filter": "wiener", "periodic": "before_each_fft", "l2": "flushed between steps",
-                       "valid_lenslets": plan.valid_count, "parallelism": "replicas (frames sharded)"},
+                       "valid_lenslets": plan.valid_count, "parallelism": "replicas (frames sharded)",
+                       "launch": {"shape": launch[0], "ctas": launch[1], "chosen_by": "fwr_plan_autotune"}},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": TRAFFIC.get(src),
                          "kernel": "fused_kernel<float,128>", "flops_per_launch": fl,

@@ -135,6 +135,20 @@ typedef enum {
 #define FWR_OPT_EXTENSION 5
 #define FWR_EXT_ZERO 0
 #define FWR_EXT_HUDGIN 1
+/*
+ * Launch shape of the FP32 FFT kernels (not part of the method: every value
+ * gives bitwise the same result, only the speed differs; fwr_plan_autotune
+ * picks them by timing).
+ *   FWR_OPT_SHAPE: 256x256 grids: the CTA's 16 warps work the slabs as one
+ *     group on 64-line slabs (1) or as two groups of 8 on 32-line slabs at
+ *     the same time (2, the default 0). N <= 128: the final filter's weights
+ *     are kept in shared memory where they fit (1, the default 0) or read from
+ *     L2 (2). Values 0..2.
+ *   FWR_OPT_CTAS: persistent CTAs of one launch, 0 (default) = every SM times
+ *     the CTAs that fit on one; a larger value is clamped to that.
+ */
+#define FWR_OPT_SHAPE 6
+#define FWR_OPT_CTAS 7
 
 /*
  * Create a plan for an n x n lenslet array (Sec. 2; Algorithm 1 input).
@@ -243,6 +257,25 @@ fwr_status fwr_reconstruct_f64(fwr_plan* plan, const double* slopes_dev, const d
 fwr_status fwr_reconstruct_host(fwr_plan* plan, const float* slopes_host, int n_frames, int iters,
                                 float* phase_host, void* stream);
 
+/*
+ * Choose the plan's launch shape (FWR_OPT_SHAPE, FWR_OPT_CTAS) by timing the
+ * candidates on the caller's data: fwr_reconstruct_ex of n_frames frames
+ * (slopes_dev, phase_dev as there) with `iters` iterations, one warm-up and
+ * three timed launches per candidate, on `stream` (synchronises it). The
+ * fastest is set on the plan and appended to the JSON-lines file cache_path
+ * (NULL: no cache) under a key of the device (name, SM count), the driver and
+ * runtime versions, the plan's geometry and options, n_frames and iters; an
+ * entry for the same key is applied without timing. Candidates: the shapes
+ * the plan's grid has (two for 256x256 and for N <= 128 when the final weights
+ * fit shared memory) times the CTA counts {all, 3/4, 1/2 of the SMs} (times
+ * the CTAs per SM). Every candidate gives bitwise the same phase.
+ */
+fwr_status fwr_plan_autotune(fwr_plan* plan, const float* slopes_dev, int n_frames, int iters, float* phase_dev,
+                             void* stream, const char* cache_path);
+/* The plan's current FWR_OPT_SHAPE and FWR_OPT_CTAS (-1 for NULL). */
+int fwr_plan_shape(const fwr_plan* plan);
+int fwr_plan_ctas(const fwr_plan* plan);
+
 /* Pre-allocate host-path staging for n_frames frames (and the copy streams). */
 fwr_status fwr_plan_reserve(fwr_plan* plan, int n_frames);
 
@@ -270,10 +303,11 @@ fwr_status fwr_plan_reserve(fwr_plan* plan, int n_frames);
  * Runs on one batch must not overlap on the GPU (shared working memory).
  * fwr_batch_schedule re-balances with `ctas` persistent CTAs (1 .. SM count)
  * and a 256x256/128x128 cost ratio; fwr_batch_autotune times candidate
- * (ctas, cost_ratio) pairs on the caller's data (synchronises `stream`),
- * keeps the fastest and appends it to the JSON-lines file cache_path (NULL:
- * no cache); a cached entry for the same device, plans, frame counts and
- * iterations is applied without timing.
+ * (ctas, cost_ratio, shape) triples on the caller's data (synchronises
+ * `stream`), keeps the fastest and appends it to the JSON-lines file
+ * cache_path (NULL: no cache); a cached entry for the same device, driver and
+ * runtime versions, plans, frame counts and iterations is applied without
+ * timing.
  */
 typedef struct fwr_batch fwr_batch;
 fwr_status fwr_batch_create(fwr_batch** out, fwr_plan* const* plans, int n_plans, const int* frame_plan,
@@ -285,6 +319,11 @@ fwr_status fwr_batch_autotune(fwr_batch* batch, const float* const* slopes_dev, 
                               void* stream, const char* cache_path);
 int fwr_batch_ctas(const fwr_batch* batch);
 double fwr_batch_cost_ratio(const fwr_batch* batch);
+/* The 256x256 frames' kernel shape (as FWR_OPT_SHAPE: 1 or 2 warp groups;
+ * default 2), also chosen by fwr_batch_autotune when a 256x256 plan is
+ * present; bitwise the same result either way. */
+int fwr_batch_shape(const fwr_batch* batch);
+fwr_status fwr_batch_set_shape(fwr_batch* batch, int shape);
 void fwr_batch_destroy(fwr_batch* batch);
 
 /*

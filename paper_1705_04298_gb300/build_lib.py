@@ -20,7 +20,7 @@ INCLUDE = os.path.join(os.path.dirname(PKG), "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 
-SOURCES = ["fwr_fused.cu", "fwr_slab.cu", "fwr_ragged.cu", "fwr_basic.cu", "fwr_net.cu", "fwr_linws.cu", "fwr_dftgemm_tc.cu", "fwr_api.cpp", "fwr_batch.cpp", "fwr_peak.cu", "fwr_anygrid.cu"]
+SOURCES = ["fwr_fused.cu", "fwr_slab.cu", "fwr_ragged.cu", "fwr_basic.cu", "fwr_net.cu", "fwr_linws.cu", "fwr_dftgemm_tc.cu", "fwr_api.cpp", "fwr_batch.cpp", "fwr_peak.cu", "fwr_anygrid.cu", "fwr_tune.cpp"]
 
 
 def nvcc():

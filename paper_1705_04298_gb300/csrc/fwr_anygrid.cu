@@ -251,6 +251,7 @@ cudaError_t launch_any(int N, const Params<T>& p, cudaStream_t s) {
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, AG_NT, smem)) != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     int grid = sms * per_sm;
+    if (p.ctas > 0 && p.ctas < grid) grid = p.ctas;
     if (grid > p.F) grid = p.F;
     kern<<<grid, AG_NT, smem, s>>>(p, N);
     return cudaGetLastError();

@@ -420,6 +420,18 @@ fwr_status fwr_plan_set_option(fwr_plan* p, int key, double value) {
         p->extension = v;
         return FWR_OK;
     }
+    if (key == FWR_OPT_SHAPE) {
+        const int v = int(value);
+        if (double(v) != value || v < 0 || v > 2) return FWR_ERR_ARG;
+        p->shape = v;
+        return FWR_OK;
+    }
+    if (key == FWR_OPT_CTAS) {
+        const int v = int(value);
+        if (double(v) != value || v < 0 || v > 65536) return FWR_ERR_ARG;
+        p->ctas = v;
+        return FWR_OK;
+    }
     if (key == FWR_OPT_PERIODIC) {
         const int v = int(value);
         if (double(v) != value || v < FWR_PERIODIC_BEFORE_EACH_FFT || v > FWR_PERIODIC_NONE) return FWR_ERR_ARG;
@@ -460,6 +472,8 @@ fwr_status fwr_reconstruct_ex(fwr_plan* p, const float* slopes, const float* ext
     k.F = n_frames;
     k.iters = iters;
     k.periodic = p->periodic;
+    k.shape = p->shape;
+    k.ctas = p->ctas;
     k.status = p->d_status;
     const bool hudgin = p->extension == FWR_EXT_HUDGIN && !ext_init;
     if (hudgin) {
@@ -536,6 +550,8 @@ fwr_status fwr_reconstruct_static(fwr_plan* p, const float* slopes, int n_frames
     k.F = n_frames;
     k.iters = iters;
     k.periodic = p->periodic;
+    k.shape = p->shape;
+    k.ctas = p->ctas;
     k.status = p->d_status;
     if (p->extension == FWR_EXT_HUDGIN) k.hud = p->d_hud;
     cudaError_t e = fwr::launch_slab_static(k, p->d_static_scratch, ctas, static_cast<cudaStream_t>(stream));
@@ -561,6 +577,8 @@ fwr_status fwr_reconstruct_f64(fwr_plan* p, const double* slopes, const double* 
     k.F = n_frames;
     k.iters = iters;
     k.periodic = p->periodic;
+    k.shape = p->shape;
+    k.ctas = p->ctas;
     k.status = p->d_status;
     if (p->extension == FWR_EXT_HUDGIN && !ext_init) {
         if (!pow2(p->N) || !fwr::fused_supported(p->N, 8, p->n)) return FWR_ERR_UNSUPPORTED;
@@ -753,6 +771,8 @@ cudaError_t fwr::launch_warm_bf16(fwr_plan* p, const float* slopes, const uint16
     k.F = n_frames;
     k.iters = iters;
     k.periodic = p->periodic;
+    k.shape = p->shape;
+    k.ctas = p->ctas;
     k.status = p->d_status;
     return fwr::launch_fused_f32(p->N, k, s);
 }

@@ -324,6 +324,7 @@ static cudaError_t launch_one(const Params<T>& p, cudaStream_t s) {
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem)) != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     int grid = sms * per_sm;
+    if (p.ctas > 0 && p.ctas < grid) grid = p.ctas;
     if (grid > p.F) grid = p.F;
     kern<<<grid, NT, smem, s>>>(p);
     return cudaGetLastError();

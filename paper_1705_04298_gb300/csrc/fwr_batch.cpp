@@ -31,6 +31,7 @@ struct fwr_batch {
     std::vector<int> frame_plan;
     int ctas = 0;
     double cost_ratio = 0;
+    int shape = 2;  // warp groups of the 256^2 path (1 or 2)
     size_t smem = 0;
     fwr::RaggedPlan* d_plans = nullptr;
     int* d_frame_plan = nullptr;
@@ -208,6 +209,7 @@ static fwr_status batch_run(fwr_batch* b, const int* frame_plan_dev, const float
     p.scratch = b->d_scratch;
     p.iters = b->iters;
     p.n_plans = int(b->plans.size());
+    p.shape = b->shape;
     cudaError_t e = fwr::launch_ragged(p, b->ctas, b->smem, static_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? FWR_OK : fwr::cuda_fail(e, "ragged launch");
 }
@@ -218,6 +220,14 @@ fwr_status fwr_batch_run(fwr_batch* b, const float* const* slopes_dev, float* co
 }
 
 int fwr_batch_ctas(const fwr_batch* b) { return b ? b->ctas : -1; }
+
+int fwr_batch_shape(const fwr_batch* b) { return b ? b->shape : -1; }
+
+fwr_status fwr_batch_set_shape(fwr_batch* b, int shape) {
+    if (!b || (shape != 1 && shape != 2)) return FWR_ERR_ARG;
+    b->shape = shape;
+    return FWR_OK;
+}
 
 double fwr_batch_cost_ratio(const fwr_batch* b) { return b ? b->cost_ratio : -1.0; }
 
@@ -244,8 +254,13 @@ fwr_status fwr_batch_autotune(fwr_batch* b, const float* const* slopes_dev, floa
     if (e != cudaSuccess) return fwr::cuda_fail(e, "fwr_batch_autotune");
     std::vector<int> counts(b->plans.size(), 0);
     for (int f : b->frame_plan) counts[f]++;
+    int drv = 0, rt = 0;
+    cudaDriverGetVersion(&drv);
+    cudaRuntimeGetVersion(&rt);
+    bool has256 = false;
+    for (const fwr_plan* pl : b->plans) has256 |= pl->N == 256;
     std::ostringstream key;
-    key << prop.name << "|sm" << b->sms;
+    key << prop.name << "|sm" << b->sms << "|drv" << drv << "|rt" << rt;
     for (size_t i = 0; i < b->plans.size(); ++i)
         key << "|N" << b->plans[i]->N << "n" << b->plans[i]->n << "v" << b->plans[i]->nvalid << "x" << counts[i];
     key << "|k" << b->iters;
@@ -257,17 +272,21 @@ fwr_status fwr_batch_autotune(fwr_batch* b, const float* const* slopes_dev, floa
     if (cache_path && cache_path[0]) {
         std::ifstream in(cache_path);
         std::string line;
-        int ctas = -1;
+        int ctas = -1, shape = 2;
         double ratio = -1;
         const std::string needle = "\"key\": \"" + k + "\"";
         while (std::getline(in, line)) {
             if (line.find(needle) == std::string::npos) continue;
-            size_t a = line.find("\"ctas\": "), r = line.find("\"cost_ratio\": ");
+            size_t a = line.find("\"ctas\": "), r = line.find("\"cost_ratio\": "), sh = line.find("\"shape\": ");
             if (a == std::string::npos || r == std::string::npos) continue;
             ctas = std::atoi(line.c_str() + a + 8);
             ratio = std::atof(line.c_str() + r + 14);
+            shape = sh == std::string::npos ? 2 : std::atoi(line.c_str() + sh + 9);
         }
-        if (ctas >= 1 && ctas <= b->sms && ratio > 0) return fwr_batch_schedule(b, ctas, ratio);
+        if (ctas >= 1 && ctas <= b->sms && ratio > 0 && (shape == 1 || shape == 2)) {
+            b->shape = shape;
+            return fwr_batch_schedule(b, ctas, ratio);
+        }
     }
 
     // otherwise time the candidates on the caller's data
@@ -280,10 +299,14 @@ fwr_status fwr_batch_autotune(fwr_batch* b, const float* const* slopes_dev, floa
     }
     const double ratios[] = {4.0, 6.0, 8.0, 9.6, 11.0, 13.0, 16.0};
     const int ctas_opts[] = {b->sms, b->sms - b->sms / 8};
+    std::vector<int> shapes = {2};
+    if (has256) shapes.push_back(1);
     double best_ms = 1e30, best_ratio = kDefaultCostRatio;
-    int best_ctas = b->sms;
+    int best_ctas = b->sms, best_shape = b->shape;
     fwr_status st = FWR_OK;
-    for (int ctas : ctas_opts) {
+    for (int shape : shapes) {
+      b->shape = shape;
+      for (int ctas : ctas_opts) {
         for (double ratio : ratios) {
             if ((st = fwr_batch_schedule(b, ctas, ratio)) != FWR_OK) break;
             if ((st = fwr_batch_run(b, slopes_dev, phase_dev, stream)) != FWR_OK) break;  // warm-up
@@ -301,18 +324,22 @@ fwr_status fwr_batch_autotune(fwr_batch* b, const float* const* slopes_dev, floa
                 best_ms = ms;
                 best_ratio = ratio;
                 best_ctas = ctas;
+                best_shape = shape;
             }
         }
         if (st != FWR_OK) break;
+      }
+      if (st != FWR_OK) break;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st != FWR_OK) return st;
+    b->shape = best_shape;
     st = fwr_batch_schedule(b, best_ctas, best_ratio);
     if (st == FWR_OK && cache_path && cache_path[0]) {
         std::ofstream o(cache_path, std::ios::app);
         o << "{\"key\": \"" << k << "\", \"ctas\": " << best_ctas << ", \"cost_ratio\": " << best_ratio
-          << ", \"ms_per_run\": " << best_ms / 3.0 << "}\n";
+          << ", \"shape\": " << best_shape << ", \"ms_per_run\": " << best_ms / 3.0 << "}\n";
     }
     return st;
 }

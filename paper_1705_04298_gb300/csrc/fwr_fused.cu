@@ -130,7 +130,7 @@ template <typename T, int N>
 cudaError_t launch_n(const Params<T>& p0, cudaStream_t s) {
     // keep the final-filter table in shared memory when it still fits
     Params<T> p = p0;
-    p.wf_smem = Layout<T, N>::bytes_wf(p.n) <= size_t(227) * 1024 ? 1 : 0;
+    p.wf_smem = p.shape != 2 && Layout<T, N>::bytes_wf(p.n) <= size_t(227) * 1024 ? 1 : 0;
     const size_t smem = p.wf_smem ? Layout<T, N>::bytes_wf(p.n) : Layout<T, N>::bytes(p.n);
     auto kern = p.hud ? fused_kernel<T, N, true> : fused_kernel<T, N, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
@@ -141,6 +141,7 @@ cudaError_t launch_n(const Params<T>& p0, cudaStream_t s) {
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 4 * N, smem)) != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     int grid = sms * per_sm;
+    if (p.ctas > 0 && p.ctas < grid) grid = p.ctas;
     if (grid > p.F) grid = p.F;
     kern<<<grid, 4 * N, smem, s>>>(p);
     return cudaGetLastError();

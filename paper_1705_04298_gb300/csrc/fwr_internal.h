@@ -39,6 +39,12 @@ template <typename T> struct Params {
     // row i the first / last pupil column, hud[2n + i] / hud[3n + i]; -1 where
     // the column or row has no pupil cell. nullptr: zero extension.
     const int16_t* hud = nullptr;
+    // kernel shape (the plan's FWR_OPT_SHAPE; results are bitwise the same for
+    // every value): 256^2 slab kernel: warp groups, 1 or 2 (0: 2); fused
+    // kernel: final-filter weights 1 = in shared memory where they fit, 2 =
+    // read from L2 (0: 1)
+    int shape = 0;
+    int ctas = 0;   // persistent CTAs (0: every SM, times the resident CTAs per SM)
 };
 
 // Where Eq. PC is applied (same values as FWR_PERIODIC_* in fwr.h).
@@ -94,10 +100,11 @@ struct RaggedParams {
     float* const* phase;
     float2* scratch;  // grid x 256^2 (only when a 256^2 plan is present)
     int iters;
+    int shape;        // warp groups of the 256^2 path (1 or 2)
     int n_plans;      // frames whose plan index is outside 0..n_plans-1 are skipped (STATUS_BADINDEX)
 };
 size_t ragged_smem_bytes(int N, int n);  // 0 if the plan cannot join a ragged batch
-cudaError_t ragged_prepare(size_t smem);
+cudaError_t ragged_prepare(size_t smem);  // both shapes
 cudaError_t launch_ragged(const RaggedParams& p, int grid, size_t smem, cudaStream_t s);
 
 // Grids of any even size 16 <= N <= 64 (fwr_anygrid.cu): direct-DFT kernel

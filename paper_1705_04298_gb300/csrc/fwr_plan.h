@@ -46,6 +46,8 @@ struct fwr_plan {
     int transform = FWR_TRANSFORM_FFT;
     int g_model = FWR_G_AVERAGED;   // measurement model of the filter tables
     int extension = FWR_EXT_ZERO;   // initial extension without a warm start
+    int shape = 0;                  // kernel shape (FWR_OPT_SHAPE)
+    int ctas = 0;                   // persistent CTAs (FWR_OPT_CTAS; 0 = every SM)
     int16_t* d_hud = nullptr;       // [4][n]: pupil edges per column and row (Hudgin extension)
     double pixel = 0.0;             // d_px / d of the filter tables
     int device = 0;

@@ -19,6 +19,7 @@ namespace fwr {
 
 static_assert(4 * 128 == SNT, "both paths of the ragged kernel run on 512 threads");
 
+template <int GROUPS>
 __global__ void __launch_bounds__(512, 1)
 ragged_kernel(RaggedParams rp) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -44,7 +45,7 @@ ragged_kernel(RaggedParams rp) {
         }
         bool ok;
         if (P.N == 128) ok = fused_frame<float, 128>(fc, rp.slopes[f], nullptr, nullptr, rp.phase[f], nullptr, rp.iters);
-        else ok = slab_frame(sc, P.tab, rp.slopes[f], nullptr, rp.phase[f], rp.iters, G);
+        else ok = slab_frame<GROUPS>(sc, P.tab, rp.slopes[f], nullptr, rp.phase[f], rp.iters, G);
         if (!ok) atomicOr(P.status, STATUS_NONFINITE);
         __syncthreads();
     }
@@ -57,11 +58,14 @@ size_t ragged_smem_bytes(int N, int n) {
 }
 
 cudaError_t ragged_prepare(size_t smem) {
-    return cudaFuncSetAttribute(ragged_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    cudaError_t e = cudaFuncSetAttribute(ragged_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(ragged_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
 }
 
 cudaError_t launch_ragged(const RaggedParams& p, int grid, size_t smem, cudaStream_t s) {
-    ragged_kernel<<<grid, 512, smem, s>>>(p);
+    if (p.shape == 1) ragged_kernel<1><<<grid, 512, smem, s>>>(p);
+    else ragged_kernel<2><<<grid, 512, smem, s>>>(p);
     return cudaGetLastError();
 }
 

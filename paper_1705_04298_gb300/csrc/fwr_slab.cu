@@ -11,6 +11,7 @@ namespace fwr {
 #include "fwr_fft.cuh"
 #include "fwr_slab.cuh"
 
+template <int GROUPS>
 __global__ void __launch_bounds__(SNT, 1)
 slab_kernel(Params<float> p, float2* scratch) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -22,15 +23,25 @@ slab_kernel(Params<float> p, float2* scratch) {
     const int nn = p.n * p.n;
     bool finite = true;
     for (int f = blockIdx.x; f < p.F; f += gridDim.x) {
-        finite &= slab_frame(c, p.tab, p.slopes + size_t(f) * 2 * nn,
-                             p.ext_init ? p.ext_init + size_t(f) * 2 * SN * SN : nullptr,
-                             p.phase + size_t(f) * SN * SN, p.iters, G, p.hud);
+        finite &= slab_frame<GROUPS>(c, p.tab, p.slopes + size_t(f) * 2 * nn,
+                                     p.ext_init ? p.ext_init + size_t(f) * 2 * SN * SN : nullptr,
+                                     p.phase + size_t(f) * SN * SN, p.iters, G, p.hud);
         __syncthreads();
     }
     if (!finite) atomicOr(&s_bad, 1);
     __syncthreads();
     if (threadIdx.x == 0 && s_bad) atomicOr(p.status, STATUS_NONFINITE);
 }
+
+namespace {
+
+// the kernel of a shape (1 or 2 warp groups; 0 is 2) with its shared-memory limit set for n
+cudaError_t slab_kernel_for(int shape, int n, void (**k)(Params<float>, float2*)) {
+    *k = shape == 1 ? slab_kernel<1> : slab_kernel<2>;
+    return cudaFuncSetAttribute(*k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(slab_layout_bytes(n)));
+}
+
+}  // namespace
 
 size_t slab_smem_bytes(int n) { return slab_layout_bytes(n); }
 
@@ -44,12 +55,14 @@ int slab_max_ctas() {
 }
 
 cudaError_t launch_slab(const Params<float>& p, float2* scratch, int max_ctas, cudaStream_t s) {
-    const size_t smem = slab_smem_bytes(p.n);
-    cudaError_t e = cudaFuncSetAttribute(slab_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    void (*kern)(Params<float>, float2*) = nullptr;
+    cudaError_t e = slab_kernel_for(p.shape, p.n, &kern);
     if (e != cudaSuccess) return e;
-    int grid = max_ctas < p.F ? max_ctas : p.F;
+    int grid = max_ctas;
+    if (p.ctas > 0 && p.ctas < grid) grid = p.ctas;
+    if (grid > p.F) grid = p.F;
     if (grid < 1) return cudaErrorInvalidConfiguration;
-    slab_kernel<<<grid, SNT, smem, s>>>(p, scratch);
+    kern<<<grid, SNT, slab_smem_bytes(p.n), s>>>(p, scratch);
     return cudaGetLastError();
 }
 
@@ -67,8 +80,9 @@ cudaError_t static_slab_prepare(int n, float2** addr) {
     void* ptr = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_slab_scratch);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(slab_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(slab_smem_bytes(n)));
-    if (e != cudaSuccess) return e;
+    void (*kern)(Params<float>, float2*) = nullptr;
+    if ((e = slab_kernel_for(1, n, &kern)) != cudaSuccess || (e = slab_kernel_for(2, n, &kern)) != cudaSuccess)
+        return e;
     *addr = static_cast<float2*>(ptr);
     return cudaSuccess;
 }
@@ -76,7 +90,8 @@ cudaError_t static_slab_prepare(int n, float2** addr) {
 cudaError_t launch_slab_static(const Params<float>& p, float2* scratch, int ctas, cudaStream_t s) {
     if (ctas < 1 || ctas > STATIC_SLAB_GRIDS || !scratch) return cudaErrorInvalidValue;
     const int grid = ctas < p.F ? ctas : p.F;
-    slab_kernel<<<grid, SNT, slab_smem_bytes(p.n), s>>>(p, scratch);
+    auto kern = p.shape == 1 ? slab_kernel<1> : slab_kernel<2>;
+    kern<<<grid, SNT, slab_smem_bytes(p.n), s>>>(p, scratch);
     return cudaGetLastError();
 }
 

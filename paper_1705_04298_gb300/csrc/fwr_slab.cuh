@@ -49,22 +49,31 @@
 namespace {
 
 constexpr int SN = 256;        // grid size
-constexpr int SL = 32;         // lines per slab
 constexpr int SNT = 512;       // threads per CTA
-constexpr int SGT = 256;       // threads per group (two groups)
 constexpr int SH = SN / 2;
-constexpr int SC = SL / 2;     // first-half columns of a column slab
-constexpr int WS = SC + 1;     // row stride of the spectral weights of a column slab
 constexpr int CLS = SN + 1;    // column phase: line stride in shared memory (cells)
 constexpr int RGS = 17;        // row phase: stride of the 16-cell groups of a line
 constexpr int RLS = 16 * RGS;  // row phase: line stride
-constexpr int LB_CELLS = SL * RLS;  // one group's buffer
-static_assert(SL * CLS <= LB_CELLS, "slab buffer");
+constexpr int SLAB_LINES = 64; // lines of all groups' slabs together
+
+// Kernel shape: GROUPS warp groups (1 or 2) of 512 / GROUPS threads, each on
+// its own slab of 64 / GROUPS lines at a time.
+template <int GROUPS> struct SlabShape {
+    static_assert(GROUPS == 1 || GROUPS == 2, "one or two groups");
+    static constexpr int SL = SLAB_LINES / GROUPS;  // lines per slab
+    static constexpr int SGT = SNT / GROUPS;        // threads per group
+    static constexpr int SC = SL / 2;               // first-half columns of a column slab
+    static constexpr int WS = SC + 1;               // row stride of a group's spectral weights
+    static constexpr int LB_CELLS = SL * RLS;       // one group's buffer
+    static_assert(SL * CLS <= LB_CELLS, "slab buffer");
+};
 
 __device__ __forceinline__ float2 conjf2(float2 a) { return make_float2(a.x, -a.y); }
 
-// barrier of one group's 256 threads (named barriers 1 and 2)
-__device__ __forceinline__ void group_sync(int g) { asm volatile("bar.sync %0, %1;\n" ::"r"(g + 1), "r"(SGT) : "memory"); }
+// barrier of one group's threads (named barrier 1 + g)
+__device__ __forceinline__ void group_sync(int g, int threads) {
+    asm volatile("bar.sync %0, %1;\n" ::"r"(g + 1), "r"(threads) : "memory");
+}
 
 // asynchronous global -> shared copies (cp.async), completed by cp_wait_all
 __device__ __forceinline__ void cp_async4(void* dst, const void* src) {
@@ -79,16 +88,18 @@ __device__ __forceinline__ void prefetch_lines_l2(const void* p, size_t bytes, i
         asm volatile("prefetch.global.L2 [%0];\n" ::"l"(b + o));
 }
 
-// storage column of line j in column slab s: j < 16 -> 16 s + j; j >= 16 ->
-// the partner -(16 s + j - 16), with the self-paired column 128 in place of
-// the duplicate 0 in slab 0
+// storage column of line j in column slab s (SC first-half columns per
+// slab): j < SC -> SC s + j; j >= SC -> the partner -(SC s + j - SC), with the
+// self-paired column 128 in place of the duplicate 0 in slab 0
+template <int SC>
 __device__ __forceinline__ int slab_col(int s, int j) {
     if (j < SC) return SC * s + j;
     const int jj = j - SC;
     return (s == 0 && jj == 0) ? SH : (SN - SC * s - jj) & (SN - 1);
 }
 // the line holding the partner column -kx of line j (self-paired: columns 0
-// and 128, lines 0 and 16 of slab 0)
+// and 128, lines 0 and SC of slab 0)
+template <int SC>
 __device__ __forceinline__ int partner_line(int s, int j) { return (s == 0 && (j & (SC - 1)) == 0) ? j : (j ^ SC); }
 
 // forward (INV = false) or inverse 16-point DFT of x with the twiddle
@@ -111,20 +122,25 @@ __device__ __forceinline__ void dft16_tw(float2 (&x)[16], const float2* tw16, in
 // Shared-memory bytes of the slab path for n lenslets: the two groups' slab
 // exchange buffers and spectral weights (256 rows x 17 columns each), the 1-D
 // tables (twiddles, a(u), T(u), the separable factors p(u)) and the mask.
+// (The weights of one group's slab take WS x SN floats; two groups of 17
+// columns need one column more than one group of 33, so the layout reserves
+// the larger.)
+constexpr int SLAB_WTS = 2 * SlabShape<2>::WS * SN > SlabShape<1>::WS * SN ? 2 * SlabShape<2>::WS * SN
+                                                                               : SlabShape<1>::WS * SN;
 __host__ __device__ __forceinline__ size_t slab_layout_bytes(int n) {
-    return 2 * size_t(LB_CELLS) * sizeof(float2) + 3 * size_t(SN) * sizeof(float2) + 256 * sizeof(float2) +
-           4 * size_t(SN) * sizeof(float) + 2 * WS * size_t(SN) * sizeof(float) + ((size_t(n) * n + 15) & ~size_t(15));
+    return size_t(SLAB_LINES) * RLS * sizeof(float2) + 3 * size_t(SN) * sizeof(float2) + 256 * sizeof(float2) +
+           4 * size_t(SN) * sizeof(float) + size_t(SLAB_WTS) * sizeof(float) + ((size_t(n) * n + 15) & ~size_t(15));
 }
 
 // Per-CTA state of the slab path for one plan.
 struct SlabCtx {
-    float2* Lb;   // two buffers of LB_CELLS
+    float2* Lb;   // the groups' buffers (64 lines of RLS cells in all)
     float2* tw;
     float2* A;
     float2* Tt;
     float2* tw16;  // w_256^(n2 k) at [k][n2], n2, k < 16
     float* pt;
-    float* wts;   // two tables of WS * SN
+    float* wts;   // the groups' weight tables (SLAB_WTS floats in all)
     uint8_t* mask;
     int n, off, nn, mode;
 };
@@ -133,13 +149,13 @@ struct SlabCtx {
 __device__ __forceinline__ void slab_setup(SlabCtx& c, unsigned char* smem, const Tables<float>& tab,
                                            const uint8_t* mask_g, int n, int off, int mode) {
     c.Lb = reinterpret_cast<float2*>(smem);
-    c.tw = c.Lb + 2 * LB_CELLS;
+    c.tw = c.Lb + SLAB_LINES * RLS;
     c.A = c.tw + SN;
     c.Tt = c.A + SN;
     c.tw16 = c.Tt + SN;
     c.pt = reinterpret_cast<float*>(c.tw16 + 256);
     c.wts = c.pt + 4 * SN;
-    c.mask = reinterpret_cast<uint8_t*>(c.wts + 2 * WS * SN);
+    c.mask = reinterpret_cast<uint8_t*>(c.wts + SLAB_WTS);
     c.n = n;
     c.off = off;
     c.nn = n * n;
@@ -163,14 +179,18 @@ __device__ __forceinline__ void slab_setup(SlabCtx& c, unsigned char* smem, cons
 // that saw a non-finite measured slope.
 //
 // Tasks: a thread works two tasks of 16 points in every pass. Column phase:
-// line t mod 32 (both tasks), pass index q = t / 32 and q + 8 (t: the
+// line t mod SL (both tasks), pass index q = t / SL and q + 8 (t: the
 // thread's index in its group). Row phase: cell group q = t mod 16 (both
-// tasks), lines t / 16 and + 16.
+// tasks), lines t / 16 and + SL / 2. Both shapes give bitwise the same
+// result (each line transform and each bin's arithmetic is the same).
+template <int GROUPS>
 __device__ __forceinline__ bool slab_frame(const SlabCtx& c, const Tables<float>& tab, const float* sl,
                                            const float* ext, float* phase, int iters, float2* G,
                                            const int16_t* hud = nullptr) {
+    typedef SlabShape<GROUPS> Sh;
+    constexpr int SL = Sh::SL, SGT = Sh::SGT, SC = Sh::SC, WS = Sh::WS;
     const int g = threadIdx.x / SGT, tg = threadIdx.x % SGT;
-    float2* const Lb = c.Lb + g * LB_CELLS;
+    float2* const Lb = c.Lb + g * Sh::LB_CELLS;
     const float2* const tw = c.tw;
     const float2* const tw16 = c.tw16;
     const float2* const A = c.A;
@@ -181,7 +201,7 @@ __device__ __forceinline__ bool slab_frame(const SlabCtx& c, const Tables<float>
     const int n = c.n, off = c.off, nn = c.nn, mode = c.mode;
     bool finite = true;
     // column-phase roles
-    const int cl = tg & (SL - 1), cq = tg >> 5;
+    const int cl = tg & (SL - 1), cq = tg / SL;
     // row-phase roles
     const int rq = tg & 15, rl = tg >> 4;
     const unsigned half_mask = 0xFFFFu << (threadIdx.x & 16);  // the 16 lanes of this row group
@@ -191,19 +211,20 @@ __device__ __forceinline__ bool slab_frame(const SlabCtx& c, const Tables<float>
         if (it >= 0) {
             // ------------------------------------------------ column phase
             const bool fill = mode == PERIODIC_BEFORE_EACH_FFT || (mode == PERIODIC_FINAL_ONLY && final);
-            for (int s = g; s < SN / SL; s += 2) {
-                const int kx = slab_col(s, cl);
-                const int pl = partner_line(s, cl);
+            for (int s = g; s < SN / SL; s += GROUPS) {
+                const int kx = slab_col<SC>(s, cl);
+                const int pl = partner_line<SC>(s, cl);
                 {
                     // spectral weights of the first-half columns: wts[ky][j] at
                     // (ky, kx) from the half-table (rows 0..N/2; (-ky, -kx) beyond);
                     // 16 lanes read 16 adjacent columns of one table row
                     const float* wt = final ? tab.wfin : tab.iota;
-                    const int j = tg & (SC - 1), kxj = slab_col(s, j), kxn = (SN - kxj) & (SN - 1);
+                    const int j = tg & (SC - 1), kxj = slab_col<SC>(s, j), kxn = (SN - kxj) & (SN - 1);
                     for (int k = tg / SC; k < SN; k += SGT / SC)
                         cp_async4(wts + k * WS + j, wt + (k <= SH ? k * SN + kxj : (SN - k) * SN + kxn));
-                    if (s == 0)  // line 16: the self-paired column 128
-                        cp_async4(wts + tg * WS + SC, wt + (tg <= SH ? tg : SN - tg) * SN + SH);
+                    if (s == 0)  // line SC: the self-paired column 128
+                        for (int k = tg; k < SN; k += SGT)
+                            cp_async4(wts + k * WS + SC, wt + (k <= SH ? k : SN - k) * SN + SH);
                 }
                 float2 x[2][16];
                 // pass A: 16-point DFTs over rows 16 n1 + n2 of the column, straight from L2
@@ -220,7 +241,7 @@ __device__ __forceinline__ bool slab_frame(const SlabCtx& c, const Tables<float>
 #pragma unroll
                     for (int k1 = 0; k1 < 16; ++k1) Lb[cl * CLS + 16 * k1 + n2] = x[i][k1];
                 }
-                group_sync(g);
+                group_sync(g, SGT);
                 // pass B: bins ky = k1 + 16 k2 of the column
 #pragma unroll
                 for (int i = 0; i < 2; ++i) {
@@ -229,7 +250,7 @@ __device__ __forceinline__ bool slab_frame(const SlabCtx& c, const Tables<float>
                     for (int n2 = 0; n2 < 16; ++n2) x[i][n2] = Lb[cl * CLS + 16 * k1 + n2];
                     dft_reg<16, false>(x[i]);
                 }
-                group_sync(g);
+                group_sync(g, SGT);
                 // the spectrum in natural order, for the partner bins
 #pragma unroll
                 for (int i = 0; i < 2; ++i) {
@@ -238,7 +259,7 @@ __device__ __forceinline__ bool slab_frame(const SlabCtx& c, const Tables<float>
                     for (int k2 = 0; k2 < 16; ++k2) Lb[cl * CLS + k1 + 16 * k2] = x[i][k2];
                 }
                 cp_wait_all();
-                group_sync(g);
+                group_sync(g, SGT);
                 // spectral step on the task's own bins (ky, kx), partner (-ky, -kx) from
                 // shared memory; then the inverse pass A on the same registers
                 float2 ey = make_float2(0.f, 0.f);
@@ -292,14 +313,14 @@ __device__ __forceinline__ bool slab_frame(const SlabCtx& c, const Tables<float>
                     // inverse pass A: the bins ky = 16 n1 + n2 with n2 = k1
                     dft16_tw<true>(x[i], tw16, k1);
                 }
-                group_sync(g);
+                group_sync(g, SGT);
 #pragma unroll
                 for (int i = 0; i < 2; ++i) {
                     const int n2 = cq + 8 * i;
 #pragma unroll
                     for (int k1 = 0; k1 < 16; ++k1) Lb[cl * CLS + 16 * k1 + n2] = x[i][k1];
                 }
-                group_sync(g);
+                group_sync(g, SGT);
                 // inverse pass B, rows k1 + 16 k2 of the column back to L2
 #pragma unroll
                 for (int i = 0; i < 2; ++i) {
@@ -310,7 +331,7 @@ __device__ __forceinline__ bool slab_frame(const SlabCtx& c, const Tables<float>
 #pragma unroll
                     for (int k2 = 0; k2 < 16; ++k2) __stcg(G + (k1 + 16 * k2) * SN + kx, x[i][k2]);
                 }
-                group_sync(g);
+                group_sync(g, SGT);
             }
             // both groups' columns are in L2 before any row is read
             __syncthreads();
@@ -318,7 +339,7 @@ __device__ __forceinline__ bool slab_frame(const SlabCtx& c, const Tables<float>
         // --------------------------------------------------------- row phase
         const bool fill_next = !final && (mode == PERIODIC_BEFORE_EACH_FFT ||
                                           (mode == PERIODIC_FINAL_ONLY && it + 1 == iters));
-        for (int b = g; b < SN / SL; b += 2) {
+        for (int b = g; b < SN / SL; b += GROUPS) {
             const int m0 = SL * b;
             {
                 // this slab's measured slopes into L2 while it is loaded and transformed
@@ -328,12 +349,12 @@ __device__ __forceinline__ bool slab_frame(const SlabCtx& c, const Tables<float>
                     prefetch_lines_l2(sl + nn + p0 * n, size_t(p1 - p0) * n * sizeof(float), tg, SGT);
                 }
             }
-            // y[i][k2]: cell (row m0 + rl + 16 i, column rq + 16 k2)
+            // y[i][k2]: cell (row m0 + rl + SL/2 i, column rq + 16 k2)
             float2 y[2][16];
             if (it < 0) {
 #pragma unroll
                 for (int i = 0; i < 2; ++i) {
-                    const int row = m0 + rl + 16 * i;
+                    const int row = m0 + rl + (SL / 2) * i;
 #pragma unroll
                     for (int k2 = 0; k2 < 16; ++k2) {
                         const int cc = rq + 16 * k2, gi = row * SN + cc;
@@ -360,22 +381,22 @@ __device__ __forceinline__ bool slab_frame(const SlabCtx& c, const Tables<float>
                 // inverse pass A: 16-point DFTs over cells 16 n1 + n2 of the row (n2 = rq)
 #pragma unroll
                 for (int i = 0; i < 2; ++i) {
-                    const int row = m0 + rl + 16 * i;
+                    const int row = m0 + rl + (SL / 2) * i;
 #pragma unroll
                     for (int n1 = 0; n1 < 16; ++n1) y[i][n1] = __ldcg(G + row * SN + 16 * n1 + rq);
                 }
 #pragma unroll
                 for (int i = 0; i < 2; ++i) {
-                    const int line = rl + 16 * i;
+                    const int line = rl + (SL / 2) * i;
                     dft16_tw<true>(y[i], tw16, rq);
 #pragma unroll
                     for (int k1 = 0; k1 < 16; ++k1) Lb[line * RLS + RGS * k1 + rq] = y[i][k1];
                 }
-                group_sync(g);
+                group_sync(g, SGT);
                 // inverse pass B: cells rq + 16 k2 of the row
 #pragma unroll
                 for (int i = 0; i < 2; ++i) {
-                    const int line = rl + 16 * i;
+                    const int line = rl + (SL / 2) * i;
 #pragma unroll
                     for (int n2 = 0; n2 < 16; ++n2) y[i][n2] = Lb[line * RLS + RGS * rq + n2];
                     dft_reg<16, true>(y[i]);
@@ -383,18 +404,18 @@ __device__ __forceinline__ bool slab_frame(const SlabCtx& c, const Tables<float>
                 if (final) {
 #pragma unroll
                     for (int i = 0; i < 2; ++i) {
-                        float* ph = phase + (m0 + rl + 16 * i) * SN + rq;
+                        float* ph = phase + (m0 + rl + (SL / 2) * i) * SN + rq;
 #pragma unroll
                         for (int k2 = 0; k2 < 16; ++k2) __stcs(ph + 16 * k2, y[i][k2].x);
                     }
-                    group_sync(g);
+                    group_sync(g, SGT);
                     continue;
                 }
             }
             // Algorithm 1 step 4 (and the embedding): the measurement in the pupil
 #pragma unroll
             for (int i = 0; i < 2; ++i) {
-                const int ii = m0 + rl + 16 * i - off;
+                const int ii = m0 + rl + (SL / 2) * i - off;
                 if (ii >= 0 && ii < n) {
 #pragma unroll
                     for (int k2 = 0; k2 < 16; ++k2) {
@@ -431,19 +452,19 @@ __device__ __forceinline__ bool slab_frame(const SlabCtx& c, const Tables<float>
                 }
             }
             // forward pass A on the same registers (cells 16 n1 + n2 with n2 = rq)
-            if (it >= 0) group_sync(g);  // every inverse pass B has read its cells
+            if (it >= 0) group_sync(g, SGT);  // every inverse pass B has read its cells
 #pragma unroll
             for (int i = 0; i < 2; ++i) {
-                const int line = rl + 16 * i;
+                const int line = rl + (SL / 2) * i;
                 dft16_tw<false>(y[i], tw16, rq);
 #pragma unroll
                 for (int k1 = 0; k1 < 16; ++k1) Lb[line * RLS + RGS * k1 + rq] = y[i][k1];
             }
-            group_sync(g);
+            group_sync(g, SGT);
             // forward pass B: cells rq + 16 k2 of the row spectrum back to L2
 #pragma unroll
             for (int i = 0; i < 2; ++i) {
-                const int line = rl + 16 * i;
+                const int line = rl + (SL / 2) * i;
 #pragma unroll
                 for (int n2 = 0; n2 < 16; ++n2) y[i][n2] = Lb[line * RLS + RGS * rq + n2];
                 dft_reg<16, false>(y[i]);
@@ -451,7 +472,7 @@ __device__ __forceinline__ bool slab_frame(const SlabCtx& c, const Tables<float>
 #pragma unroll
                 for (int k2 = 0; k2 < 16; ++k2) __stcg(gp + 16 * k2, y[i][k2]);
             }
-            group_sync(g);
+            group_sync(g, SGT);
         }
         // both groups' rows are in L2 before the next column phase (or the next frame)
         __syncthreads();

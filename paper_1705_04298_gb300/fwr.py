@@ -27,6 +27,8 @@ OPT_PIXEL = 4
 G_AVERAGED = 0
 G_FRIED = 1
 OPT_EXTENSION = 5
+OPT_SHAPE = 6
+OPT_CTAS = 7
 EXT_ZERO = 0
 EXT_HUDGIN = 1
 TRANSFORM_FFT = 0
@@ -56,6 +58,11 @@ SIGNATURES = {
     "fwr_reconstruct_host": (_I, [_P, _P, _I, _I, _P, _P]),
     "fwr_reconstruct_static": (_I, [_P, _P, _I, _I, _P, _I, _P]),
     "fwr_plan_reserve": (_I, [_P, _I]),
+    "fwr_plan_autotune": (_I, [_P, _P, _I, _I, _P, _P, ctypes.c_char_p]),
+    "fwr_plan_shape": (_I, [_P]),
+    "fwr_plan_ctas": (_I, [_P]),
+    "fwr_batch_shape": (_I, [_P]),
+    "fwr_batch_set_shape": (_I, [_P, _I]),
     "fwr_fft2": (_I, [_I, _P, _P, _I, _I, _P]),
     "fwr_dft2_bf16x3": (_I, [_I, _P, _P, _I, _I, _P]),
     "fwr_batch_create": (_I, [ctypes.POINTER(_P), _P, _I, _P, _I, _I]),
@@ -191,6 +198,34 @@ class Plan:
         """EXT_ZERO (default) or EXT_HUDGIN: the slopes outside the pupil
         before the first iteration when no warm start is given."""
         _check(self._lib.fwr_plan_set_option(self._h, OPT_EXTENSION, float(mode)), "fwr_plan_set_option")
+
+    def set_shape(self, shape):
+        """Launch shape (FWR_OPT_SHAPE, 0..2; bitwise the same result)."""
+        _check(self._lib.fwr_plan_set_option(self._h, OPT_SHAPE, float(shape)), "fwr_plan_set_option")
+
+    def set_ctas(self, ctas):
+        """Persistent CTAs of a launch (FWR_OPT_CTAS; 0 = every SM)."""
+        _check(self._lib.fwr_plan_set_option(self._h, OPT_CTAS, float(ctas)), "fwr_plan_set_option")
+
+    @property
+    def shape(self):
+        return self._lib.fwr_plan_shape(self._h)
+
+    @property
+    def ctas(self):
+        return self._lib.fwr_plan_ctas(self._h)
+
+    def autotune(self, slopes, iters, phase, cache_path=None, stream=None):
+        """Time the launch shapes on these frames and keep the fastest
+        (fwr_plan_autotune); returns (shape, ctas)."""
+        import torch
+        F = slopes.shape[0]
+        _need(slopes, torch.float32, (F, 2, self.n, self.n), "slopes")
+        _need(phase, torch.float32, (F, self.N, self.N), "phase")
+        path = None if cache_path is None else str(cache_path).encode()
+        _check(self._lib.fwr_plan_autotune(self._h, _ptr(slopes), F, int(iters), _ptr(phase), _stream(stream), path),
+               "fwr_plan_autotune")
+        return self.shape, self.ctas
 
     def set_transform(self, mode):
         """TRANSFORM_FFT (default) or TRANSFORM_DFT_BF16X3 (tensor-core split-BF16
@@ -350,6 +385,13 @@ class Batch:
     @property
     def ctas(self):
         return self._lib.fwr_batch_ctas(self._h)
+
+    @property
+    def shape(self):
+        return self._lib.fwr_batch_shape(self._h)
+
+    def set_shape(self, shape):
+        _check(self._lib.fwr_batch_set_shape(self._h, int(shape)), "fwr_batch_set_shape")
 
     @property
     def cost_ratio(self):
