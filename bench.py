@@ -337,6 +337,18 @@ def extra_measurements(fwr, synth, torch, flush):
     tf = flops_per_frame(256, 10) * 1000 / (ms / 1e3) / 1e12
     res["128x128_256grid_k10_frozen_flow"] = {"frames_per_s": 1000 / (ms / 1e3), "ms": ms, "tflops": tf,
                                               "frac": tf / peak, "launch": {"shape": launch4[0], "ctas": launch4[1]}}
+    # ELT scale: 200x200 lenslets on 512^2 (slab kernel, grid in HBM), k = 10
+    sl5, _, m5 = synth.batch(200, 16, 7000, 0.05)
+    p5 = fwr.Plan(m5, 2.56, fwr.LSQ)
+    F5 = 2 * torch.cuda.get_device_properties(0).multi_processor_count
+    s5 = torch.tensor(sl5, dtype=torch.float32, device="cuda").repeat(F5 // 16 + 1, 1, 1, 1)[:F5].contiguous()
+    ph5 = torch.empty((F5, 512, 512), device="cuda")
+    launch5 = p5.autotune(s5, 10, ph5, os.path.join(OUT_DIR, "fwr_plan_tune.jsonl"))
+    ms = _time_launches(lambda: p5.reconstruct(s5, 10, ph5), flush, 3, torch)
+    tf = flops_per_frame(512, 10) * F5 / (ms / 1e3) / 1e12
+    res["200x200_512grid_k10"] = {"frames": F5, "frames_per_s": F5 / (ms / 1e3), "ms": ms, "tflops": tf,
+                                  "frac": tf / peak, "launch": {"shape": launch5[0], "ctas": launch5[1]}}
+    del s5, ph5
     # the same frames through the split-BF16 DFT-as-GEMM transform (batched
     # tcgen05 GEMMs): 2 GEMMs per 2-D transform, 2 (k + 1) transforms, each
     # GEMM 2 x (2N) x (6N) x N flop per frame
@@ -516,7 +528,7 @@ def run_reference(args):
     return 0
 
 
-WORKLOADS = ("fused128", "slab256", "dftgemm256", "unet", "linws")
+WORKLOADS = ("fused128", "slab256", "slab512", "dftgemm256", "unet", "linws")
 
 
 def run_workload(args):
@@ -526,6 +538,7 @@ def run_workload(args):
     calls on seeded synthetic frames (--frames, 1000 by default):
       fused128    40x40 lenslets on 128^2, Wiener, --iters iterations
       slab256     128x128 lenslets on 256^2 (frozen-flow frames), LSQ, --iters
+      slab512     200x200 lenslets on 512^2 (ELT scale, seeded frames), LSQ, --iters
       dftgemm256  the same through the split-BF16 DFT-as-GEMM transform
       unet        the warm-start U-Net forward on 40x40 slopes (committed weights)
       linws       the linear warm start (--rank) alone, then with --iters
@@ -551,6 +564,12 @@ def run_workload(args):
         s = torch.tensor(sl, dtype=torch.float32, device="cuda").repeat((F + 31) // 32, 1, 1, 1)[:F].contiguous()
         out = torch.empty((F, plan.N, plan.N), device="cuda")
         runs.append(("%s_k%d" % (args.workload, k), lambda: plan.reconstruct(s, k, out)))
+    elif args.workload == "slab512":
+        sl, _, mask = synth.batch(200, 16, 7000, 0.05)
+        plan = fwr.Plan(mask, 2.56, fwr.LSQ)
+        s = torch.tensor(sl, dtype=torch.float32, device="cuda").repeat((F + 15) // 16, 1, 1, 1)[:F].contiguous()
+        out = torch.empty((F, plan.N, plan.N), device="cuda")
+        runs.append(("slab512_k%d" % k, lambda: plan.reconstruct(s, k, out)))
     elif args.workload == "unet":
         net = learned.load_net(fwr, learned.WEIGHTS, max_batch=F)
         plan = learned.make_plan(fwr, fwr.WIENER, learned.EVAL_SIGMA)

@@ -186,7 +186,7 @@ fwr::Tables<T> view(const fwr::DevTables<T>& d) {
     return t;
 }
 
-bool supported_grid(int N) { return N == 16 || N == 32 || N == 64 || N == 128 || N == 256; }
+bool supported_grid(int N) { return N == 16 || N == 32 || N == 64 || N == 128 || N == 256 || N == 512; }
 
 
 bool pow2(int N) { return N > 0 && (N & (N - 1)) == 0; }
@@ -287,17 +287,17 @@ fwr_status plan_create_n(fwr_plan** out, int n, int N, const uint8_t* pupil_mask
         st = upload_tables<float>(h, N, p->f32);
         if (st == FWR_OK && N <= 64) st = upload_tables<double>(h, N, p->f64);
     }
-    if (st == FWR_OK && N == 256) {
-        if (fwr::slab_smem_bytes(n) > size_t(227) * 1024) {
+    if (st == FWR_OK && N >= 256) {
+        if (fwr::slab_smem_bytes(N, n) > size_t(227) * 1024) {
             st = FWR_ERR_UNSUPPORTED;
         } else {
             p->scratch_ctas = fwr::slab_max_ctas();
-            const size_t b = size_t(p->scratch_ctas) * fwr::slab_scratch_elems_per_cta() * sizeof(float2);
+            const size_t b = size_t(p->scratch_ctas) * fwr::slab_scratch_elems_per_cta(N) * sizeof(float2);
             if ((e = cudaMalloc(&p->d_scratch, b)) != cudaSuccess) st = cuda_fail(e, "cudaMalloc scratch");
             // the static array of fwr_reconstruct_static: its address on this
             // device, looked up now so that the allocation-free call itself
             // loads nothing; a failure here only disables that entry point
-            if (st == FWR_OK && fwr::static_slab_prepare(n, &p->d_static_scratch) != cudaSuccess) {
+            if (st == FWR_OK && N == 256 && fwr::static_slab_prepare(n, &p->d_static_scratch) != cudaSuccess) {
                 p->d_static_scratch = nullptr;
                 cudaGetLastError();
             }
@@ -478,7 +478,7 @@ fwr_status fwr_reconstruct_ex(fwr_plan* p, const float* slopes, const float* ext
     const bool hudgin = p->extension == FWR_EXT_HUDGIN && !ext_init;
     if (hudgin) {
         if (p->transform == FWR_TRANSFORM_DFT_BF16X3 || !pow2(p->N) ||
-            (p->N != 256 && !fwr::fused_supported(p->N, 4, p->n)))
+            (p->N < 256 && !fwr::fused_supported(p->N, 4, p->n)))
             return FWR_ERR_UNSUPPORTED;
         k.hud = p->d_hud;
     }
@@ -492,9 +492,9 @@ fwr_status fwr_reconstruct_ex(fwr_plan* p, const float* slopes, const float* ext
         } else {
             e = fwr::launch_basic_gemm_f32(p->N, k, static_cast<cudaStream_t>(stream));
         }
-    } else if (p->N == 256) {
+    } else if (p->N >= 256) {
         if (ext_out || !phase) return FWR_ERR_UNSUPPORTED;
-        e = fwr::launch_slab(k, p->d_scratch, p->scratch_ctas, static_cast<cudaStream_t>(stream));
+        e = fwr::launch_slab(p->N, k, p->d_scratch, p->scratch_ctas, static_cast<cudaStream_t>(stream));
     } else {
         e = fwr::fused_supported(p->N, 4, p->n) ? fwr::launch_fused_f32(p->N, k, static_cast<cudaStream_t>(stream))
                                                 : fwr::launch_basic_f32(p->N, k, static_cast<cudaStream_t>(stream));
@@ -758,7 +758,7 @@ const char* fwr_last_error(void) { return g_last_error; }
 
 cudaError_t fwr::launch_warm_bf16(fwr_plan* p, const float* slopes, const uint16_t* ext_init_h, int n_frames,
                                   int iters, float* phase, cudaStream_t s) {
-    if (p->transform != FWR_TRANSFORM_FFT || p->N == 256 || !fwr::fused_supported(p->N, 4, p->n))
+    if (p->transform != FWR_TRANSFORM_FFT || p->N >= 256 || !fwr::fused_supported(p->N, 4, p->n))
         return cudaErrorNotSupported;
     fwr::Params<float> k;
     k.tab = view(p->f32);

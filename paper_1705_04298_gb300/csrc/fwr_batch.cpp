@@ -153,7 +153,7 @@ fwr_status fwr_batch_create(fwr_batch** out, fwr_plan* const* plans, int n_plans
                                          cudaMemcpyHostToDevice)) != cudaSuccess) ||
         (e = cudaMalloc(&b->d_off, sizeof(int) * (b->sms + 1))) != cudaSuccess ||
         (e = cudaMalloc(&b->d_order, sizeof(int) * std::max(1, n_frames))) != cudaSuccess ||
-        (need_scratch && (e = cudaMalloc(&b->d_scratch, size_t(b->sms) * fwr::slab_scratch_elems_per_cta() *
+        (need_scratch && (e = cudaMalloc(&b->d_scratch, size_t(b->sms) * fwr::slab_scratch_elems_per_cta(256) *
                                                             sizeof(float2))) != cudaSuccess) ||
         (e = fwr::ragged_prepare(smem)) != cudaSuccess) {
         st = fwr::cuda_fail(e, "fwr_batch_create");

@@ -66,13 +66,14 @@ cudaError_t launch_basic_gemm_f32(int N, const Params<float>& p, cudaStream_t s)
 cudaError_t launch_dft2_gemm_f32(int N, const float2* in, float2* out, int F, int inverse, const float2* tw,
                                  cudaStream_t s);
 
-// 256^2 grids (fwr_slab.cu): the grid lives in a per-CTA global scratch area
-// of slab_scratch_elems_per_cta() float2 and is streamed through shared
-// memory. launch_slab uses at most max_ctas CTAs (scratch must hold that many).
-size_t slab_smem_bytes(int n);
-size_t slab_scratch_elems_per_cta();
+// 256^2 and 512^2 grids (fwr_slab.cu): the grid lives in a per-CTA global
+// scratch area of slab_scratch_elems_per_cta(N) float2 and is streamed
+// through shared memory. launch_slab uses at most max_ctas CTAs (scratch must
+// hold that many).
+size_t slab_smem_bytes(int N, int n);
+size_t slab_scratch_elems_per_cta(int N);
 int slab_max_ctas();
-cudaError_t launch_slab(const Params<float>& p, float2* scratch, int max_ctas, cudaStream_t s);
+cudaError_t launch_slab(int N, const Params<float>& p, float2* scratch, int max_ctas, cudaStream_t s);
 // The same kernel on the library's static scratch array (no allocation):
 // at most STATIC_SLAB_GRIDS CTAs; cudaErrorInvalidValue for ctas outside
 // 1..STATIC_SLAB_GRIDS. static_slab_prepare (current device) returns the

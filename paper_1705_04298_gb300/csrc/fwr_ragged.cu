@@ -40,12 +40,12 @@ ragged_kernel(RaggedParams rp) {
         const RaggedPlan P = rp.plans[pl];
         if (pl != cur) {
             if (P.N == 128) fused_setup<float, 128>(fc, smem, P.tab, P.mask, P.n, P.off, P.periodic);
-            else slab_setup(sc, smem, P.tab, P.mask, P.n, P.off, P.periodic);
+            else slab_setup<256>(sc, smem, P.tab, P.mask, P.n, P.off, P.periodic);
             cur = pl;
         }
         bool ok;
         if (P.N == 128) ok = fused_frame<float, 128>(fc, rp.slopes[f], nullptr, nullptr, rp.phase[f], nullptr, rp.iters);
-        else ok = slab_frame<GROUPS>(sc, P.tab, rp.slopes[f], nullptr, rp.phase[f], rp.iters, G);
+        else ok = slab_frame<256, GROUPS>(sc, P.tab, rp.slopes[f], nullptr, rp.phase[f], rp.iters, G);
         if (!ok) atomicOr(P.status, STATUS_NONFINITE);
         __syncthreads();
     }

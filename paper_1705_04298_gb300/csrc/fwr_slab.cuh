@@ -3,69 +3,101 @@
 // namespace fwr after fwr_fft.cuh.
 #pragma once
 
-// Gerchberg kernel for 256^2 grids (sm_103a): slab-streamed through shared memory.
+// Gerchberg kernel for 256^2 and 512^2 grids (sm_103a): slab-streamed through
+// shared memory.
 //
-// A 256 x 256 complex grid (512 KB) does not fit one SM's shared memory, so
-// each persistent CTA keeps its frame's packed grid Z = sx + i sy in its own
-// area of a global scratch buffer (L2 resident: 512 KB per CTA) and works it
-// in slabs of 32 lines:
+// An SN x SN complex grid (512 KB at SN = 256, 2 MB at 512) does not fit one
+// SM's shared memory, so each persistent CTA keeps its frame's packed grid
+// Z = sx + i sy in its own area of a global scratch buffer (L2 resident at
+// 256^2; HBM at 512^2) and works it in slabs of lines:
 //
-//   row phase, 8 slabs of 32 rows:     inverse row FFTs, reinsertion of the
-//                                      measured slopes (Algorithm 1 step 4),
-//                                      x part of the periodic fill (Eq. PC),
-//                                      forward row FFTs
-//   column phase, 8 slabs of 32 cols:  forward column FFTs, y part of Eq. PC
-//                                      as a spectral correction, the LSQ
-//                                      projection (Sec. 3.3) or the final
-//                                      filter (Eqs. 2-3), inverse column FFTs
+//   row phase, slabs of rows:     inverse row FFTs, reinsertion of the
+//                                 measured slopes (Algorithm 1 step 4),
+//                                 x part of the periodic fill (Eq. PC),
+//                                 forward row FFTs
+//   column phase, slabs of cols:  forward column FFTs, y part of Eq. PC as a
+//                                 spectral correction, the LSQ projection
+//                                 (Sec. 3.3) or the final filter (Eqs. 2-3),
+//                                 inverse column FFTs
 //
-// Column slab s holds the columns kx in [16 s, 16 s + 16) and their partners
-// -kx (slab 0 also holds the self-paired column 128), so every (k, -k) pair of
-// the spectral step lies in one slab.
+// Column slab s holds SC first-half columns kx in [SC s, SC s + SC) and their
+// partners -kx (slab 0 also holds the self-paired column SN/2), so every
+// (k, -k) pair of the spectral step lies in one slab.
 //
-// The CTA's 16 warps form two groups of 8 that work different slabs of the
-// same phase at the same time (group g takes slabs g, g + 2, ...), each with
-// its own shared-memory buffer and named barrier, so one group's L2 loads
+// The CTA's 16 warps form one group or two groups of 8 (the launch shape)
+// that work different slabs of the same phase at the same time, each with its
+// own shared-memory buffer and named barrier, so one group's memory loads
 // overlap the other's arithmetic; a CTA barrier separates the phases.
 //
-// 256-point line FFTs: two register passes (four-step), 16-point DFTs over
-// elements 16 apart with twiddles w_256^(n2 k1), then 16-point DFTs over the
-// other index. A task keeps 16 points of one line. The slab data move
-// between the scratch area (L2) and registers directly (coalesced 8-byte
-// loads and stores: the lanes of a warp take adjacent columns in the column
-// phase, 16 adjacent cells of a row in the row phase), and shared memory is
-// used only for the exchanges between the passes:
-//   column phase: L2 -> pass A -> smem -> pass B -> smem (the partner bins of
-//     the spectral step) -> spectral step and inverse pass A in registers ->
-//     smem -> inverse pass B -> L2;
-//   row phase: L2 -> inverse pass A -> smem -> inverse pass B, reinsertion,
-//     x fill (row sums by warp shuffles) and forward pass A in registers (the
-//     inverse pass B leaves each task the cells the forward pass A needs) ->
-//     smem -> pass B -> L2.
+// SN-point line FFTs, SN = 16 RB (RB = 16 or 32): two register passes
+// (four-step). Forward: 16-point DFTs over elements RB apart with twiddles
+// w_SN^(n2 k1), then RB-point DFTs (output k1 + 16 k2). Inverse, in the
+// transposed order: RB-point DFTs over elements 16 apart with the conjugate
+// twiddles, then 16-point DFTs (output k1 + RB k2). So the forward transform
+// leaves each task exactly the elements the inverse one starts from, and the
+// inverse transform each task the elements the forward one starts from. The
+// slab data move between the scratch area and registers directly (coalesced
+// 8-byte loads and stores: the lanes of a warp take adjacent columns in the
+// column phase, 16 or 32 adjacent cells of a row in the row phase), and
+// shared memory is used only for the exchanges between the passes:
+//   column phase: memory -> pass A -> smem -> pass B -> smem (the partner
+//     bins of the spectral step) -> spectral step and inverse pass A in
+//     registers -> smem -> inverse pass B -> memory;
+//   row phase: memory -> inverse pass A -> smem -> inverse pass B,
+//     reinsertion, x fill (row sums by warp shuffles) and forward pass A in
+//     registers -> smem -> pass B -> memory.
 // That is six crossings of shared memory per column slab and four per row
-// slab. Column-phase exchanges use lines 257 cells apart, row-phase ones
-// groups of 16 cells 17 apart: both bank-conflict free.
+// slab. Column-phase exchanges use lines SN + 1 cells apart, row-phase ones
+// groups of 16 or RB cells padded by one: all bank-conflict free.
 
 namespace {
 
-constexpr int SN = 256;        // grid size
 constexpr int SNT = 512;       // threads per CTA
-constexpr int SH = SN / 2;
-constexpr int CLS = SN + 1;    // column phase: line stride in shared memory (cells)
-constexpr int RGS = 17;        // row phase: stride of the 16-cell groups of a line
-constexpr int RLS = 16 * RGS;  // row phase: line stride
-constexpr int SLAB_LINES = 64; // lines of all groups' slabs together
+constexpr int SN = 256;        // the grid of the static-scratch entry point and of ragged batches
 
-// Kernel shape: GROUPS warp groups (1 or 2) of 512 / GROUPS threads, each on
-// its own slab of 64 / GROUPS lines at a time.
-template <int GROUPS> struct SlabShape {
+// Kernel shape of grid N: GROUPS warp groups (1 or 2) of 512 / GROUPS threads,
+// each on its own slab of SL lines at a time.
+template <int N, int GROUPS> struct SlabShape {
+    static_assert(N == 256 || N == 512, "grid");
     static_assert(GROUPS == 1 || GROUPS == 2, "one or two groups");
-    static constexpr int SL = SLAB_LINES / GROUPS;  // lines per slab
-    static constexpr int SGT = SNT / GROUPS;        // threads per group
-    static constexpr int SC = SL / 2;               // first-half columns of a column slab
-    static constexpr int WS = SC + 1;               // row stride of a group's spectral weights
-    static constexpr int LB_CELLS = SL * RLS;       // one group's buffer
-    static_assert(SL * CLS <= LB_CELLS, "slab buffer");
+    static constexpr int RB = N / 16;                       // size of the long pass
+    static constexpr int H = N / 2;
+    static constexpr int SL = (N == 256 ? 64 : 32) / GROUPS;  // lines per slab
+    static constexpr int SGT = SNT / GROUPS;                // threads per group
+    static constexpr int SC = SL / 2;                       // first-half columns of a column slab
+    static constexpr int WS = SC + 1;                       // row stride of a group's spectral weights
+    static constexpr int CLS = N + 1;                       // column phase: line stride (cells)
+    static constexpr int RLS_I = RB * 17;                   // row phase, inverse: groups of 16, stride 17
+    static constexpr int RLS_F = 16 * (RB + 1);             // row phase, forward: groups of RB, stride RB + 1
+    static constexpr int M1 = SL * CLS > SL * RLS_I ? SL * CLS : SL * RLS_I;
+    static constexpr int LB_CELLS = M1 > SL * RLS_F ? M1 : SL * RLS_F;  // one group's buffer
+    static constexpr int NA = SL * RB / SGT;                // 16-point tasks per thread and pass
+    static constexpr int NB = SL * 16 / SGT;                // RB-point tasks per thread and pass
+    static_assert(NA * SGT == SL * RB && NB * SGT == SL * 16, "tasks divide evenly");
+};
+
+// Shared-memory layout of the slab path for grid N (the larger shape's
+// buffers and weights): bytes, and where each table starts.
+template <int N> struct SlabLayout {
+    typedef SlabShape<N, 1> S1;
+    typedef SlabShape<N, 2> S2;
+    static constexpr int RB = N / 16;
+    static constexpr size_t lb = 0;
+    static constexpr size_t LB_BYTES =
+        (size_t(S1::LB_CELLS) > 2 * size_t(S2::LB_CELLS) ? size_t(S1::LB_CELLS) : 2 * size_t(S2::LB_CELLS)) * 8;
+    static constexpr size_t tw = lb + LB_BYTES;             // N cells: w_N^j
+    static constexpr size_t a = tw + size_t(N) * 8;         // N cells: a(u)
+    static constexpr size_t t = a + size_t(N) * 8;          // N cells: T(u)
+    static constexpr size_t twa = t + size_t(N) * 8;        // 16 x RB cells: w_N^(n2 k1) at [k1][n2]
+    static constexpr size_t twi = twa + size_t(16) * RB * 8;  // RB x 16 cells: w_N^(n2 k1) at [k1][n2]
+    static constexpr size_t pt = twi + size_t(16) * RB * 8;   // 4 N floats
+    static constexpr size_t WTS = 2 * size_t(S2::WS) * N > size_t(S1::WS) * N ? 2 * size_t(S2::WS) * N
+                                                                               : size_t(S1::WS) * N;
+    static constexpr size_t wts = pt + size_t(4) * N * 4;
+    static constexpr size_t mask = wts + WTS * 4;           // n x n bytes (256^2 only; 512^2 reads global)
+    __host__ __device__ static size_t bytes(int n) {
+        return mask + (N == 256 ? ((size_t(n) * n + 15) & ~size_t(15)) : 0);
+    }
 };
 
 __device__ __forceinline__ float2 conjf2(float2 a) { return make_float2(a.x, -a.y); }
@@ -90,173 +122,187 @@ __device__ __forceinline__ void prefetch_lines_l2(const void* p, size_t bytes, i
 
 // storage column of line j in column slab s (SC first-half columns per
 // slab): j < SC -> SC s + j; j >= SC -> the partner -(SC s + j - SC), with the
-// self-paired column 128 in place of the duplicate 0 in slab 0
-template <int SC>
+// self-paired column N/2 in place of the duplicate 0 in slab 0
+template <int N, int SC>
 __device__ __forceinline__ int slab_col(int s, int j) {
     if (j < SC) return SC * s + j;
     const int jj = j - SC;
-    return (s == 0 && jj == 0) ? SH : (SN - SC * s - jj) & (SN - 1);
+    return (s == 0 && jj == 0) ? N / 2 : (N - SC * s - jj) & (N - 1);
 }
 // the line holding the partner column -kx of line j (self-paired: columns 0
-// and 128, lines 0 and SC of slab 0)
+// and N/2, lines 0 and SC of slab 0)
 template <int SC>
 __device__ __forceinline__ int partner_line(int s, int j) { return (s == 0 && (j & (SC - 1)) == 0) ? j : (j ^ SC); }
 
-// forward (INV = false) or inverse 16-point DFT of x with the twiddle
-// w_256^(n2 k) (conjugated for the inverse) applied to output k; tw16 holds
-// w_256^(n2 k) at [k][n2], so lanes with consecutive n2 read consecutive
-// entries (the row phase) and lanes with one n2 read one entry (the column
-// phase): no bank conflicts either way
-template <bool INV>
-__device__ __forceinline__ void dft16_tw(float2 (&x)[16], const float2* tw16, int n2) {
-    dft_reg<16, INV>(x);
+// forward (INV = false) or inverse R-point DFT of x with the twiddle tws[k]
+// (conjugated for the inverse) applied to output k; tws points at the
+// task's column of a [k][n2] table with row stride `stride`
+template <int R, bool INV>
+__device__ __forceinline__ void dft_tw(float2 (&x)[R], const float2* tws, int stride) {
+    dft_reg<R, INV>(x);
 #pragma unroll
-    for (int k = 1; k < 16; ++k) {
-        const float2 w = tw16[16 * k + n2];
+    for (int k = 1; k < R; ++k) {
+        const float2 w = tws[stride * k];
         x[k] = INV ? cmulc(w, x[k]) : cmul(x[k], w);
     }
 }
 
 }  // namespace
 
-// Shared-memory bytes of the slab path for n lenslets: the two groups' slab
-// exchange buffers and spectral weights (256 rows x 17 columns each), the 1-D
-// tables (twiddles, a(u), T(u), the separable factors p(u)) and the mask.
-// (The weights of one group's slab take WS x SN floats; two groups of 17
-// columns need one column more than one group of 33, so the layout reserves
-// the larger.)
-constexpr int SLAB_WTS = 2 * SlabShape<2>::WS * SN > SlabShape<1>::WS * SN ? 2 * SlabShape<2>::WS * SN
-                                                                               : SlabShape<1>::WS * SN;
-__host__ __device__ __forceinline__ size_t slab_layout_bytes(int n) {
-    return size_t(SLAB_LINES) * RLS * sizeof(float2) + 3 * size_t(SN) * sizeof(float2) + 256 * sizeof(float2) +
-           4 * size_t(SN) * sizeof(float) + size_t(SLAB_WTS) * sizeof(float) + ((size_t(n) * n + 15) & ~size_t(15));
+// Shared-memory bytes of the slab path for grid N (256 or 512) and n lenslets.
+__host__ __device__ __forceinline__ size_t slab_layout_bytes_n(int N, int n) {
+    return N == 512 ? SlabLayout<512>::bytes(n) : SlabLayout<256>::bytes(n);
 }
+__host__ __device__ __forceinline__ size_t slab_layout_bytes(int n) { return SlabLayout<256>::bytes(n); }
 
 // Per-CTA state of the slab path for one plan.
 struct SlabCtx {
-    float2* Lb;   // the groups' buffers (64 lines of RLS cells in all)
-    float2* tw;
+    float2* Lb;    // the groups' buffers
+    float2* tw;    // w_N^j
     float2* A;
     float2* Tt;
-    float2* tw16;  // w_256^(n2 k) at [k][n2], n2, k < 16
+    float2* twa;   // w_N^(n2 k1) at [k1][n2], k1 < 16, n2 < RB (forward pass A)
+    float2* twi;   // w_N^(n2 k1) at [k1][n2], k1 < RB, n2 < 16 (inverse pass A)
     float* pt;
-    float* wts;   // the groups' weight tables (SLAB_WTS floats in all)
-    uint8_t* mask;
+    float* wts;    // the groups' weight tables
+    const uint8_t* mask;  // shared memory (256^2) or the plan's global copy (512^2)
     int n, off, nn, mode;
 };
 
-// Load a plan's 1-D tables and mask into shared memory; ends with a barrier.
+// Load a plan's 1-D tables (and at 256^2 the mask) into shared memory; ends
+// with a barrier.
+template <int N>
 __device__ __forceinline__ void slab_setup(SlabCtx& c, unsigned char* smem, const Tables<float>& tab,
                                            const uint8_t* mask_g, int n, int off, int mode) {
-    c.Lb = reinterpret_cast<float2*>(smem);
-    c.tw = c.Lb + SLAB_LINES * RLS;
-    c.A = c.tw + SN;
-    c.Tt = c.A + SN;
-    c.tw16 = c.Tt + SN;
-    c.pt = reinterpret_cast<float*>(c.tw16 + 256);
-    c.wts = c.pt + 4 * SN;
-    c.mask = reinterpret_cast<uint8_t*>(c.wts + SLAB_WTS);
+    typedef SlabLayout<N> L;
+    constexpr int RB = N / 16;
+    c.Lb = reinterpret_cast<float2*>(smem + L::lb);
+    c.tw = reinterpret_cast<float2*>(smem + L::tw);
+    c.A = reinterpret_cast<float2*>(smem + L::a);
+    c.Tt = reinterpret_cast<float2*>(smem + L::t);
+    c.twa = reinterpret_cast<float2*>(smem + L::twa);
+    c.twi = reinterpret_cast<float2*>(smem + L::twi);
+    c.pt = reinterpret_cast<float*>(smem + L::pt);
+    c.wts = reinterpret_cast<float*>(smem + L::wts);
     c.n = n;
     c.off = off;
     c.nn = n * n;
     c.mode = mode;
     const int tid = threadIdx.x;
-    for (int i = tid; i < SN; i += SNT) {
+    for (int i = tid; i < N; i += SNT) {
         c.tw[i] = tab.tw[i];
         c.A[i] = tab.A[i];
         c.Tt[i] = tab.Tt[i];
     }
-    for (int i = tid; i < 4 * SN; i += SNT) c.pt[i] = tab.pt[i];
-    if (tid < 256) c.tw16[tid] = tab.tw[(tid & 15) * (tid >> 4)];
+    for (int i = tid; i < 4 * N; i += SNT) c.pt[i] = tab.pt[i];
+    for (int i = tid; i < 16 * RB; i += SNT) {
+        c.twa[i] = tab.tw[(i % RB) * (i / RB)];  // [k1][n2], k1 < 16
+        c.twi[i] = tab.tw[(i % 16) * (i / 16)];  // [k1][n2], n2 < 16
+    }
+    if (N == 256) {
+        uint8_t* m = smem + L::mask;
 #pragma unroll 8
-    for (int i = tid; i < c.nn; i += SNT) c.mask[i] = mask_g[i];
+        for (int i = tid; i < c.nn; i += SNT) m[i] = mask_g[i];
+        c.mask = m;
+    } else {
+        c.mask = mask_g;
+    }
     __syncthreads();
 }
 
-// One frame through the whole path with the grid in G (this CTA's 256^2
+// One frame through the whole path with the grid in G (this CTA's N^2
 // scratch area). sl: [2][n][n] slopes; ext: [2][N][N] warm start or nullptr;
 // phase: [N][N] output. Called by every thread; returns false in the threads
 // that saw a non-finite measured slope.
 //
-// Tasks: a thread works two tasks of 16 points in every pass. Column phase:
-// line t mod SL (both tasks), pass index q = t / SL and q + 8 (t: the
-// thread's index in its group). Row phase: cell group q = t mod 16 (both
-// tasks), lines t / 16 and + SL / 2. Both shapes give bitwise the same
+// Tasks (t: the thread's index in its group, i: its task): column phase,
+// line t mod SL and pass index q = t / SL + (SGT / SL) i; row phase, 16-cell
+// tasks (inverse pass B, forward pass A) take index t mod RB and line
+// t / RB + (SGT / RB) i, RB-cell tasks (inverse pass A, forward pass B) index
+// t mod 16 and line t / 16 + (SGT / 16) i. Both shapes give bitwise the same
 // result (each line transform and each bin's arithmetic is the same).
-template <int GROUPS>
+template <int N, int GROUPS>
 __device__ __forceinline__ bool slab_frame(const SlabCtx& c, const Tables<float>& tab, const float* sl,
                                            const float* ext, float* phase, int iters, float2* G,
                                            const int16_t* hud = nullptr) {
-    typedef SlabShape<GROUPS> Sh;
-    constexpr int SL = Sh::SL, SGT = Sh::SGT, SC = Sh::SC, WS = Sh::WS;
+    typedef SlabShape<N, GROUPS> Sh;
+    constexpr int SL = Sh::SL, SGT = Sh::SGT, SC = Sh::SC, WS = Sh::WS, RB = Sh::RB, H = Sh::H;
+    constexpr int CLS = Sh::CLS, RLS_I = Sh::RLS_I, RLS_F = Sh::RLS_F, NA = Sh::NA, NB = Sh::NB;
     const int g = threadIdx.x / SGT, tg = threadIdx.x % SGT;
     float2* const Lb = c.Lb + g * Sh::LB_CELLS;
     const float2* const tw = c.tw;
-    const float2* const tw16 = c.tw16;
+    const float2* const twa = c.twa;
+    const float2* const twi = c.twi;
     const float2* const A = c.A;
     const float2* const Tt = c.Tt;
     const float* const pt = c.pt;
-    float* const wts = c.wts + g * WS * SN;
+    float* const wts = c.wts + g * WS * N;
     const uint8_t* const mask = c.mask;
     const int n = c.n, off = c.off, nn = c.nn, mode = c.mode;
     bool finite = true;
-    // column-phase roles
-    const int cl = tg & (SL - 1), cq = tg / SL;
+    // column-phase roles: line cl, pass index cq + (SGT / SL) i
+    const int cl = tg % SL, cq = tg / SL;
+    constexpr int CQS = SGT / SL;
     // row-phase roles
-    const int rq = tg & 15, rl = tg >> 4;
-    const unsigned half_mask = 0xFFFFu << (threadIdx.x & 16);  // the 16 lanes of this row group
+    const int r16 = tg % 16, l16 = tg / 16;   // RB-cell tasks
+    const int rrb = tg % RB, lrb = tg / RB;   // 16-cell tasks
+    constexpr int L16S = SGT / 16, LRBS = SGT / RB;
+    // the RB lanes of one row's 16-cell tasks (for the x-fill row sums)
+    const unsigned row_mask = RB == 32 ? 0xFFFFFFFFu : (0xFFFFu << (threadIdx.x & 16));
     // it = -1: embed; it = 0 .. iters-1: Gerchberg; it = iters: final
     for (int it = -1; it <= iters; ++it) {
         const bool final = it == iters;
         if (it >= 0) {
             // ------------------------------------------------ column phase
             const bool fill = mode == PERIODIC_BEFORE_EACH_FFT || (mode == PERIODIC_FINAL_ONLY && final);
-            for (int s = g; s < SN / SL; s += GROUPS) {
-                const int kx = slab_col<SC>(s, cl);
+            for (int s = g; s < N / SL; s += GROUPS) {
+                const int kx = slab_col<N, SC>(s, cl);
                 const int pl = partner_line<SC>(s, cl);
                 {
                     // spectral weights of the first-half columns: wts[ky][j] at
-                    // (ky, kx) from the half-table (rows 0..N/2; (-ky, -kx) beyond);
-                    // 16 lanes read 16 adjacent columns of one table row
+                    // (ky, kx) from the half-table (rows 0..N/2; (-ky, -kx) beyond)
                     const float* wt = final ? tab.wfin : tab.iota;
-                    const int j = tg & (SC - 1), kxj = slab_col<SC>(s, j), kxn = (SN - kxj) & (SN - 1);
-                    for (int k = tg / SC; k < SN; k += SGT / SC)
-                        cp_async4(wts + k * WS + j, wt + (k <= SH ? k * SN + kxj : (SN - k) * SN + kxn));
-                    if (s == 0)  // line SC: the self-paired column 128
-                        for (int k = tg; k < SN; k += SGT)
-                            cp_async4(wts + k * WS + SC, wt + (k <= SH ? k : SN - k) * SN + SH);
+                    const int j = tg % SC, kxj = slab_col<N, SC>(s, j), kxn = (N - kxj) & (N - 1);
+                    for (int k = tg / SC; k < N; k += SGT / SC)
+                        cp_async4(wts + k * WS + j, wt + (k <= H ? k * N + kxj : (N - k) * N + kxn));
+                    if (s == 0)  // line SC: the self-paired column N/2
+                        for (int k = tg; k < N; k += SGT)
+                            cp_async4(wts + k * WS + SC, wt + (k <= H ? k : N - k) * N + H);
                 }
-                float2 x[2][16];
-                // pass A: 16-point DFTs over rows 16 n1 + n2 of the column, straight from L2
+                // pass A: 16-point DFTs over rows RB n1 + n2 of the column, from memory
+                {
+                    float2 x[NA][16];
 #pragma unroll
-                for (int i = 0; i < 2; ++i) {
-                    const int n2 = cq + 8 * i;
+                    for (int i = 0; i < NA; ++i) {
+                        const int n2 = cq + CQS * i;
 #pragma unroll
-                    for (int n1 = 0; n1 < 16; ++n1) x[i][n1] = __ldcg(G + (16 * n1 + n2) * SN + kx);
-                }
+                        for (int n1 = 0; n1 < 16; ++n1) x[i][n1] = __ldcg(G + (RB * n1 + n2) * N + kx);
+                    }
 #pragma unroll
-                for (int i = 0; i < 2; ++i) {
-                    const int n2 = cq + 8 * i;
-                    dft16_tw<false>(x[i], tw16, n2);
+                    for (int i = 0; i < NA; ++i) {
+                        const int n2 = cq + CQS * i;
+                        dft_tw<16, false>(x[i], twa + n2, RB);
 #pragma unroll
-                    for (int k1 = 0; k1 < 16; ++k1) Lb[cl * CLS + 16 * k1 + n2] = x[i][k1];
+                        for (int k1 = 0; k1 < 16; ++k1) Lb[cl * CLS + RB * k1 + n2] = x[i][k1];
+                    }
                 }
                 group_sync(g, SGT);
                 // pass B: bins ky = k1 + 16 k2 of the column
+                float2 y[NB][RB];
 #pragma unroll
-                for (int i = 0; i < 2; ++i) {
-                    const int k1 = cq + 8 * i;
+                for (int i = 0; i < NB; ++i) {
+                    const int k1 = cq + CQS * i;
 #pragma unroll
-                    for (int n2 = 0; n2 < 16; ++n2) x[i][n2] = Lb[cl * CLS + 16 * k1 + n2];
-                    dft_reg<16, false>(x[i]);
+                    for (int n2 = 0; n2 < RB; ++n2) y[i][n2] = Lb[cl * CLS + RB * k1 + n2];
+                    dft_reg<RB, false>(y[i]);
                 }
                 group_sync(g, SGT);
                 // the spectrum in natural order, for the partner bins
 #pragma unroll
-                for (int i = 0; i < 2; ++i) {
-                    const int k1 = cq + 8 * i;
+                for (int i = 0; i < NB; ++i) {
+                    const int k1 = cq + CQS * i;
 #pragma unroll
-                    for (int k2 = 0; k2 < 16; ++k2) Lb[cl * CLS + k1 + 16 * k2] = x[i][k2];
+                    for (int k2 = 0; k2 < RB; ++k2) Lb[cl * CLS + k1 + 16 * k2] = y[i][k2];
                 }
                 cp_wait_all();
                 group_sync(g, SGT);
@@ -272,14 +318,14 @@ __device__ __forceinline__ bool slab_frame(const SlabCtx& c, const Tables<float>
                 const float2 Akx = A[kx], Tkx = Tt[kx];
                 // weight column of this line and whether its rows are mirrored
                 const bool first = cl < SC || (s == 0 && cl == SC);
-                const int wcol = (s == 0 && cl == SC) ? SC : (cl & (SC - 1));
+                const int wcol = (s == 0 && cl == SC) ? SC : (cl % SC);
 #pragma unroll
-                for (int i = 0; i < 2; ++i) {
-                    const int k1 = cq + 8 * i;
+                for (int i = 0; i < NB; ++i) {
+                    const int k1 = cq + CQS * i;
 #pragma unroll
-                    for (int k2 = 0; k2 < 16; ++k2) {
-                        const int ky = k1 + 16 * k2, kyn = (SN - ky) & (SN - 1);
-                        float2 z1 = x[i][k2], z2 = Lb[pl * CLS + kyn];
+                    for (int k2 = 0; k2 < RB; ++k2) {
+                        const int ky = k1 + 16 * k2, kyn = (N - ky) & (N - 1);
+                        float2 z1 = y[i][k2], z2 = Lb[pl * CLS + kyn];
                         if (fill) {
                             // y part of Eq. PC: Z(k) -= i c, Z(-k) -= i conj(c),
                             // c = Sy(0, kx) e^{2 i pi ky / N}
@@ -298,7 +344,7 @@ __device__ __forceinline__ bool slab_frame(const SlabCtx& c, const Tables<float>
                             const float a = h1 + h2 + Py, br = h1 - h2, bi = Px;
                             const float ox = a * z1.x + br * z2.x + bi * z2.y;
                             const float oy = a * z1.y + bi * z2.x - br * z2.y;
-                            x[i][k2] = make_float2(w * ox, w * oy);
+                            y[i][k2] = make_float2(w * ox, w * oy);
                         } else {
                             // Eq. 2 with the final filter: phi = w (conj(Gx) Sx + conj(Gy) Sy)
                             const float2 z2c = conjf2(z2);
@@ -307,39 +353,42 @@ __device__ __forceinline__ bool slab_frame(const SlabCtx& c, const Tables<float>
                             const float2 gx = cmul(Akx, Tt[ky]);
                             const float2 gy = cmul(Tkx, A[ky]);
                             const float2 ph = cadd(cmulc(gx, sx), cmulc(gy, sy));
-                            x[i][k2] = make_float2(ph.x * w, ph.y * w);
+                            y[i][k2] = make_float2(ph.x * w, ph.y * w);
                         }
                     }
                     // inverse pass A: the bins ky = 16 n1 + n2 with n2 = k1
-                    dft16_tw<true>(x[i], tw16, k1);
+                    dft_tw<RB, true>(y[i], twi + k1, 16);
                 }
                 group_sync(g, SGT);
 #pragma unroll
-                for (int i = 0; i < 2; ++i) {
-                    const int n2 = cq + 8 * i;
+                for (int i = 0; i < NB; ++i) {
+                    const int n2 = cq + CQS * i;
 #pragma unroll
-                    for (int k1 = 0; k1 < 16; ++k1) Lb[cl * CLS + 16 * k1 + n2] = x[i][k1];
+                    for (int k1 = 0; k1 < RB; ++k1) Lb[cl * CLS + 16 * k1 + n2] = y[i][k1];
                 }
                 group_sync(g, SGT);
-                // inverse pass B, rows k1 + 16 k2 of the column back to L2
+                // inverse pass B, rows k1 + RB k2 of the column back to memory
+                {
+                    float2 x[NA][16];
 #pragma unroll
-                for (int i = 0; i < 2; ++i) {
-                    const int k1 = cq + 8 * i;
+                    for (int i = 0; i < NA; ++i) {
+                        const int k1 = cq + CQS * i;
 #pragma unroll
-                    for (int n2 = 0; n2 < 16; ++n2) x[i][n2] = Lb[cl * CLS + 16 * k1 + n2];
-                    dft_reg<16, true>(x[i]);
+                        for (int n2 = 0; n2 < 16; ++n2) x[i][n2] = Lb[cl * CLS + 16 * k1 + n2];
+                        dft_reg<16, true>(x[i]);
 #pragma unroll
-                    for (int k2 = 0; k2 < 16; ++k2) __stcg(G + (k1 + 16 * k2) * SN + kx, x[i][k2]);
+                        for (int k2 = 0; k2 < 16; ++k2) __stcg(G + (k1 + RB * k2) * N + kx, x[i][k2]);
+                    }
                 }
                 group_sync(g, SGT);
             }
-            // both groups' columns are in L2 before any row is read
+            // both groups' columns are in memory before any row is read
             __syncthreads();
         }
         // --------------------------------------------------------- row phase
         const bool fill_next = !final && (mode == PERIODIC_BEFORE_EACH_FFT ||
                                           (mode == PERIODIC_FINAL_ONLY && it + 1 == iters));
-        for (int b = g; b < SN / SL; b += GROUPS) {
+        for (int b = g; b < N / SL; b += GROUPS) {
             const int m0 = SL * b;
             {
                 // this slab's measured slopes into L2 while it is loaded and transformed
@@ -349,18 +398,18 @@ __device__ __forceinline__ bool slab_frame(const SlabCtx& c, const Tables<float>
                     prefetch_lines_l2(sl + nn + p0 * n, size_t(p1 - p0) * n * sizeof(float), tg, SGT);
                 }
             }
-            // y[i][k2]: cell (row m0 + rl + SL/2 i, column rq + 16 k2)
-            float2 y[2][16];
+            // x[i][k2]: cell (row m0 + lrb + LRBS i, column rrb + RB k2)
+            float2 x[NA][16];
             if (it < 0) {
 #pragma unroll
-                for (int i = 0; i < 2; ++i) {
-                    const int row = m0 + rl + (SL / 2) * i;
+                for (int i = 0; i < NA; ++i) {
+                    const int row = m0 + lrb + LRBS * i;
 #pragma unroll
                     for (int k2 = 0; k2 < 16; ++k2) {
-                        const int cc = rq + 16 * k2, gi = row * SN + cc;
+                        const int cc = rrb + RB * k2, gi = row * N + cc;
                         float2 v = make_float2(0.f, 0.f);
                         if (ext) {
-                            v = make_float2(ext[gi], ext[SN * SN + gi]);
+                            v = make_float2(ext[gi], ext[N * N + gi]);
                         } else if (hud) {
                             // Hudgin extension from the measured slopes of the pupil
                             // edges (the pupil cells are overwritten below)
@@ -374,39 +423,42 @@ __device__ __forceinline__ bool slab_frame(const SlabCtx& c, const Tables<float>
                                 if (le >= 0 && (j < le || j > rt)) v.y = __ldg(sl + nn + ii * n + (j < le ? le : rt));
                             }
                         }
-                        y[i][k2] = v;
+                        x[i][k2] = v;
                     }
                 }
             } else {
-                // inverse pass A: 16-point DFTs over cells 16 n1 + n2 of the row (n2 = rq)
+                // inverse pass A: RB-point DFTs over cells 16 n1 + n2 of the row (n2 = r16)
+                {
+                    float2 y[NB][RB];
 #pragma unroll
-                for (int i = 0; i < 2; ++i) {
-                    const int row = m0 + rl + (SL / 2) * i;
+                    for (int i = 0; i < NB; ++i) {
+                        const int row = m0 + l16 + L16S * i;
 #pragma unroll
-                    for (int n1 = 0; n1 < 16; ++n1) y[i][n1] = __ldcg(G + row * SN + 16 * n1 + rq);
-                }
+                        for (int n1 = 0; n1 < RB; ++n1) y[i][n1] = __ldcg(G + row * N + 16 * n1 + r16);
+                    }
 #pragma unroll
-                for (int i = 0; i < 2; ++i) {
-                    const int line = rl + (SL / 2) * i;
-                    dft16_tw<true>(y[i], tw16, rq);
+                    for (int i = 0; i < NB; ++i) {
+                        const int line = l16 + L16S * i;
+                        dft_tw<RB, true>(y[i], twi + r16, 16);
 #pragma unroll
-                    for (int k1 = 0; k1 < 16; ++k1) Lb[line * RLS + RGS * k1 + rq] = y[i][k1];
+                        for (int k1 = 0; k1 < RB; ++k1) Lb[line * RLS_I + 17 * k1 + r16] = y[i][k1];
+                    }
                 }
                 group_sync(g, SGT);
-                // inverse pass B: cells rq + 16 k2 of the row
+                // inverse pass B: cells rrb + RB k2 of the row
 #pragma unroll
-                for (int i = 0; i < 2; ++i) {
-                    const int line = rl + (SL / 2) * i;
+                for (int i = 0; i < NA; ++i) {
+                    const int line = lrb + LRBS * i;
 #pragma unroll
-                    for (int n2 = 0; n2 < 16; ++n2) y[i][n2] = Lb[line * RLS + RGS * rq + n2];
-                    dft_reg<16, true>(y[i]);
+                    for (int n2 = 0; n2 < 16; ++n2) x[i][n2] = Lb[line * RLS_I + 17 * rrb + n2];
+                    dft_reg<16, true>(x[i]);
                 }
                 if (final) {
 #pragma unroll
-                    for (int i = 0; i < 2; ++i) {
-                        float* ph = phase + (m0 + rl + (SL / 2) * i) * SN + rq;
+                    for (int i = 0; i < NA; ++i) {
+                        float* ph = phase + (m0 + lrb + LRBS * i) * N + rrb;
 #pragma unroll
-                        for (int k2 = 0; k2 < 16; ++k2) __stcs(ph + 16 * k2, y[i][k2].x);
+                        for (int k2 = 0; k2 < 16; ++k2) __stcs(ph + RB * k2, x[i][k2].x);
                     }
                     group_sync(g, SGT);
                     continue;
@@ -414,17 +466,17 @@ __device__ __forceinline__ bool slab_frame(const SlabCtx& c, const Tables<float>
             }
             // Algorithm 1 step 4 (and the embedding): the measurement in the pupil
 #pragma unroll
-            for (int i = 0; i < 2; ++i) {
-                const int ii = m0 + rl + (SL / 2) * i - off;
+            for (int i = 0; i < NA; ++i) {
+                const int ii = m0 + lrb + LRBS * i - off;
                 if (ii >= 0 && ii < n) {
 #pragma unroll
                     for (int k2 = 0; k2 < 16; ++k2) {
-                        const int j = rq + 16 * k2 - off;
+                        const int j = rrb + RB * k2 - off;
                         if (j >= 0 && j < n) {
                             const float vx = __ldg(sl + ii * n + j), vy = __ldg(sl + nn + ii * n + j);
                             if (mask[ii * n + j]) {
                                 if (it < 0) finite &= isfinite(vx) && isfinite(vy);
-                                y[i][k2] = make_float2(vx, vy);
+                                x[i][k2] = make_float2(vx, vy);
                             }
                         }
                     }
@@ -432,49 +484,50 @@ __device__ __forceinline__ bool slab_frame(const SlabCtx& c, const Tables<float>
             }
             if (fill_next) {
                 // x part of Eq. PC: the row's last cell takes minus the sum of the
-                // other 255; the row's 16 tasks are 16 adjacent lanes
+                // other N - 1; the row's RB tasks are RB adjacent lanes
 #pragma unroll
-                for (int i = 0; i < 2; ++i) {
+                for (int i = 0; i < NA; ++i) {
                     float t[16];
 #pragma unroll
-                    for (int k2 = 0; k2 < 16; ++k2) t[k2] = y[i][k2].x;
-                    if (rq == 15) t[15] = 0.f;
+                    for (int k2 = 0; k2 < 16; ++k2) t[k2] = x[i][k2].x;
+                    if (rrb == RB - 1) t[15] = 0.f;
 #pragma unroll
                     for (int h = 8; h >= 1; h /= 2)
 #pragma unroll
                         for (int k = 0; k < h; ++k) t[k] += t[k + h];
                     float sum = t[0];
-                    sum += __shfl_xor_sync(half_mask, sum, 1);
-                    sum += __shfl_xor_sync(half_mask, sum, 2);
-                    sum += __shfl_xor_sync(half_mask, sum, 4);
-                    sum += __shfl_xor_sync(half_mask, sum, 8);
-                    if (rq == 15) y[i][15].x = -sum;
+#pragma unroll
+                    for (int o = 1; o < RB; o *= 2) sum += __shfl_xor_sync(row_mask, sum, o);
+                    if (rrb == RB - 1) x[i][15].x = -sum;
                 }
             }
-            // forward pass A on the same registers (cells 16 n1 + n2 with n2 = rq)
+            // forward pass A on the same registers (cells RB n1 + n2 with n2 = rrb)
             if (it >= 0) group_sync(g, SGT);  // every inverse pass B has read its cells
 #pragma unroll
-            for (int i = 0; i < 2; ++i) {
-                const int line = rl + (SL / 2) * i;
-                dft16_tw<false>(y[i], tw16, rq);
+            for (int i = 0; i < NA; ++i) {
+                const int line = lrb + LRBS * i;
+                dft_tw<16, false>(x[i], twa + rrb, RB);
 #pragma unroll
-                for (int k1 = 0; k1 < 16; ++k1) Lb[line * RLS + RGS * k1 + rq] = y[i][k1];
+                for (int k1 = 0; k1 < 16; ++k1) Lb[line * RLS_F + (RB + 1) * k1 + rrb] = x[i][k1];
             }
             group_sync(g, SGT);
-            // forward pass B: cells rq + 16 k2 of the row spectrum back to L2
+            // forward pass B: cells r16 + 16 k2 of the row spectrum back to memory
+            {
+                float2 y[NB][RB];
 #pragma unroll
-            for (int i = 0; i < 2; ++i) {
-                const int line = rl + (SL / 2) * i;
+                for (int i = 0; i < NB; ++i) {
+                    const int line = l16 + L16S * i;
 #pragma unroll
-                for (int n2 = 0; n2 < 16; ++n2) y[i][n2] = Lb[line * RLS + RGS * rq + n2];
-                dft_reg<16, false>(y[i]);
-                float2* const gp = G + (m0 + line) * SN + rq;
+                    for (int n2 = 0; n2 < RB; ++n2) y[i][n2] = Lb[line * RLS_F + (RB + 1) * r16 + n2];
+                    dft_reg<RB, false>(y[i]);
+                    float2* const gp = G + (m0 + line) * N + r16;
 #pragma unroll
-                for (int k2 = 0; k2 < 16; ++k2) __stcg(gp + 16 * k2, y[i][k2]);
+                    for (int k2 = 0; k2 < RB; ++k2) __stcg(gp + 16 * k2, y[i][k2]);
+                }
             }
             group_sync(g, SGT);
         }
-        // both groups' rows are in L2 before the next column phase (or the next frame)
+        // both groups' rows are in memory before the next column phase (or the next frame)
         __syncthreads();
     }
     return finite;

@@ -58,7 +58,7 @@ def test_invalid_plans_rejected_before_device_work(lib):
     assert _create(lib, n=16, nv=-1.0)[0] == ARG
     assert _create(lib, n=16, filt=1, r0=0.0)[0] == ARG
     assert _create(lib, n=16, filt=1, L0=-3.0)[0] == ARG
-    assert _create(lib, n=200, pad=2.0)[0] == UNSUP        # N = 512
+    assert _create(lib, n=300, pad=2.0)[0] == UNSUP        # N = 1024
     code, h = _create(lib, n=16)
     assert code == 0 or code == 3  # plan needs a device; without one it is a CUDA error
     if code == 0:

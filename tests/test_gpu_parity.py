@@ -307,6 +307,50 @@ def test_256_grid_persistent_tail_and_limits(fwr):
                          ext_out=torch.empty((1, 2, 256, 256), device="cuda"))
 
 
+# ------------------------------------ 512^2 grids (ELT scale, slab kernel) --
+
+@pytest.mark.parametrize("n,pad,k,periodic,filt", [
+    (200, 2.56, 2, 0, "wiener"),
+    (160, 3.2, 1, 2, "lsq"),
+    (256, 2.0, 1, 1, "lsq"),
+])
+def test_512_grid(fwr, n, pad, k, periodic, filt):
+    """ELT-scale grids (the paper's case for the method, Sec. 1 and the
+    operation count of Sec. 3.3): 160 to 256 lenslets across on 512^2, both
+    launch shapes bitwise equal, against the FP64 oracle."""
+    r0p, L0p = synth.pitch_units(n, 0.15, 25.0)
+    sigma = 0.05
+    F = 2
+    sl, _, mask = synth.batch(n, F, 5000 + n, sigma)
+    plan = make_plan(fwr, mask, pad, fwr.WIENER if filt == "wiener" else fwr.LSQ, sigma ** 2, r0p, L0p,
+                     periodic)
+    assert plan.N == 512
+    s = torch.tensor(sl, dtype=torch.float32, device="cuda")
+    ph = plan.reconstruct(s, k).clone()
+    plan.set_shape(1)
+    assert torch.equal(plan.reconstruct(s, k), ph)
+    ph = ph.cpu().numpy()
+    for f in range(F):
+        ref, _ = run_oracle(sl[f], mask, pad, k, FILTERS[filt], sigma ** 2, r0p, L0p, periodic)
+        assert within(ph[f], ref, FP32_TOL, where="N=512 f=%d" % f)
+    assert plan.status() == "FWR_OK"
+
+
+def test_512_grid_hudgin_and_tail(fwr):
+    n, pad, k = 200, 2.56, 0
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    F = sms + 3
+    sl, _, mask = synth.batch(n, 4, 5500, 0.05)
+    s = torch.tensor(sl, dtype=torch.float32, device="cuda").repeat(F // 4 + 1, 1, 1, 1)[:F].contiguous()
+    plan = make_plan(fwr, mask, pad, fwr.LSQ)
+    plan.set_extension(fwr.EXT_HUDGIN)
+    ph = plan.reconstruct(s, k)
+    torch.cuda.synchronize()
+    assert torch.equal(ph[0], ph[sms])  # same input in the first and the last wave
+    ref, _ = oracle.reconstruct(sl[0], mask, pad, k, oracle.FILTER_LSQ, ext_init="hudgin")
+    assert within(ph[0].cpu().numpy(), ref, FP32_TOL, where="N=512 hudgin")
+
+
 def test_misaligned_phase_and_warm_start_are_refused(fwr):
     """The kernels store the phase and read the warm start with 16-byte
     vector accesses; pointers off that alignment are argument errors."""
