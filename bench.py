@@ -362,6 +362,17 @@ def extra_measurements(fwr, synth, torch, flush):
         "roofline": {"bound": "tensor", "achieved": gfl / (ms / 1e3) / 1e12, "peak": bpeak, "peak_source": bsrc,
                      "unit": "TFLOP/s", "frac": gfl / (ms / 1e3) / 1e12 / bpeak, "flops_per_launch": gfl,
                      "note": "GEMM flops only; element-wise kernels between the GEMMs are not counted"}}
+    # the same with the three-way split, six products (K = 12N)
+    p4.set_transform(fwr.TRANSFORM_DFT_BF16X6)
+    p4.reconstruct(s4, 10, ph4)
+    ms6 = _time_launches(lambda: p4.reconstruct(s4, 10, ph4), flush, 3, torch)
+    gfl6 = 2 * gfl
+    res["128x128_256grid_k10_frozen_flow_dft_bf16x6"] = {
+        "frames_per_s": 1000 / (ms6 / 1e3), "ms": ms6,
+        "roofline": {"bound": "tensor", "achieved": gfl6 / (ms6 / 1e3) / 1e12, "peak": bpeak, "peak_source": bsrc,
+                     "unit": "TFLOP/s", "frac": gfl6 / (ms6 / 1e3) / 1e12 / bpeak, "flops_per_launch": gfl6,
+                     "note": "GEMM flops only (K = 12N); element-wise kernels between the GEMMs are not counted"}}
+    p4.set_transform(fwr.TRANSFORM_FFT)
     return res
 
 

@@ -90,7 +90,17 @@ typedef enum {
                                        allocates the plan's workspace (about 170 MB) and the
                                        reconstruct calls allocate nothing; no ext_out (returns
                                        FWR_ERR_UNSUPPORTED). Other N: FWR_ERR_UNSUPPORTED.
-                                       About 1e-5 relative phase error (stated by the tests) */
+                                       About 2e-5 relative phase error (stated by the tests) */
+#define FWR_TRANSFORM_DFT_BF16X6 2  /* the batched tcgen05 DFT-as-GEMM path of N = 128 and 256
+                                       with a three-way BF16 split (x = hi + mid + lo) and six
+                                       products (hh + hm + mh + hl + mm + lh) over K = 12N: twice
+                                       the GEMM work of DFT_BF16X3 for the same measured error
+                                       (about 2e-5: the tensor core's FP32 accumulation over K,
+                                       not the operand split, sets it). Other N:
+                                       FWR_ERR_UNSUPPORTED.
+                                       Setting it allocates its own workspace (about 280 MB at
+                                       256^2), replacing a DFT_BF16X3 one (the plan falls back to
+                                       the FFT transform if that allocation fails) */
 /* Values of FWR_OPT_PERIODIC: where Eq. PC is applied. */
 #define FWR_PERIODIC_BEFORE_EACH_FFT 0 /* before every forward FFT, the final one included (default) */
 #define FWR_PERIODIC_FINAL_ONLY 1      /* once, before the final reconstruction (Algorithm 1 step 5) */

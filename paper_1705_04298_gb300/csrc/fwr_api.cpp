@@ -394,19 +394,35 @@ fwr_status fwr_plan_set_option(fwr_plan* p, int key, double value) {
     }
     if (key == FWR_OPT_TRANSFORM) {
         const int v = int(value);
-        if (double(v) != value || (v != FWR_TRANSFORM_FFT && v != FWR_TRANSFORM_DFT_BF16X3)) return FWR_ERR_ARG;
+        if (double(v) != value ||
+            (v != FWR_TRANSFORM_FFT && v != FWR_TRANSFORM_DFT_BF16X3 && v != FWR_TRANSFORM_DFT_BF16X6))
+            return FWR_ERR_ARG;
         if (v == FWR_TRANSFORM_DFT_BF16X3 && p->N != 32 && p->N != 64 && p->N != 128 && p->N != 256)
             return FWR_ERR_UNSUPPORTED;  // (non-power-of-two grids included)
-        if (v == FWR_TRANSFORM_DFT_BF16X3 && p->N >= 128 && !p->d_dftws) {
-            // batched tensor-core path: its workspace is made here, not in the reconstruct calls
+        if (v == FWR_TRANSFORM_DFT_BF16X6 && p->N != 128 && p->N != 256) return FWR_ERR_UNSUPPORTED;
+        const int terms = v == FWR_TRANSFORM_DFT_BF16X6 ? 6 : 3;
+        if (v != FWR_TRANSFORM_FFT && p->N >= 128 && (!p->d_dftws || p->dftws_terms != terms)) {
+            // batched tensor-core path: its workspace is made here, not in the
+            // reconstruct calls (one for the other product count is freed first,
+            // after a device synchronisation)
             int prev = 0;
             cudaGetDevice(&prev);
             cudaSetDevice(p->device);
-            cudaError_t e = cudaMalloc(&p->d_dftws, fwr::dftgemm_ws_bytes(p->N));
-            if (e == cudaSuccess) e = fwr::dftgemm_setup(p->N, p->f32.tw, p->d_dftws);
+            cudaError_t e = cudaSuccess;
+            if (p->d_dftws) {
+                e = cudaDeviceSynchronize();
+                cudaFree(p->d_dftws);
+                p->d_dftws = nullptr;
+                p->dftws_terms = 0;
+                if (p->transform != FWR_TRANSFORM_FFT) p->transform = FWR_TRANSFORM_FFT;
+            }
+            if (e == cudaSuccess) e = cudaMalloc(&p->d_dftws, fwr::dftgemm_ws_bytes(p->N, terms));
+            if (e == cudaSuccess) e = fwr::dftgemm_setup(p->N, terms, p->f32.tw, p->d_dftws);
             if (e != cudaSuccess) {
                 cudaFree(p->d_dftws);
                 p->d_dftws = nullptr;
+            } else {
+                p->dftws_terms = terms;
             }
             cudaSetDevice(prev);
             if (e != cudaSuccess) return cuda_fail(e, "DFT-GEMM workspace");
@@ -477,7 +493,7 @@ fwr_status fwr_reconstruct_ex(fwr_plan* p, const float* slopes, const float* ext
     k.status = p->d_status;
     const bool hudgin = p->extension == FWR_EXT_HUDGIN && !ext_init;
     if (hudgin) {
-        if (p->transform == FWR_TRANSFORM_DFT_BF16X3 || !pow2(p->N) ||
+        if (p->transform != FWR_TRANSFORM_FFT || !pow2(p->N) ||
             (p->N < 256 && !fwr::fused_supported(p->N, 4, p->n)))
             return FWR_ERR_UNSUPPORTED;
         k.hud = p->d_hud;
@@ -485,10 +501,10 @@ fwr_status fwr_reconstruct_ex(fwr_plan* p, const float* slopes, const float* ext
     cudaError_t e;
     if (!pow2(p->N)) {
         e = fwr::launch_anygrid_f32(p->N, k, static_cast<cudaStream_t>(stream));
-    } else if (p->transform == FWR_TRANSFORM_DFT_BF16X3) {
+    } else if (p->transform != FWR_TRANSFORM_FFT) {
         if (p->N >= 128) {
             if (ext_out || !phase) return FWR_ERR_UNSUPPORTED;
-            e = fwr::launch_dftgemm_f32(p->N, k, p->d_dftws, static_cast<cudaStream_t>(stream));
+            e = fwr::launch_dftgemm_f32(p->N, p->dftws_terms, k, p->d_dftws, static_cast<cudaStream_t>(stream));
         } else {
             e = fwr::launch_basic_gemm_f32(p->N, k, static_cast<cudaStream_t>(stream));
         }

@@ -6,11 +6,18 @@
 //
 // The frames of a chunk are the columns of two GEMMs per 2-D transform (D =
 // A B^T, fwr_umma.cuh). A complex N x N product is one real 2N x 2N product:
-// [Re; Im] <- [[Fr, -Fi], [Fi, Fr]] [Re; Im]. Every FP32 operand x is split as
-// hi + lo (hi = bf16(x), lo = bf16(x - hi)) and the three products hi hi +
-// hi lo + lo hi are one GEMM over K = 6N: A = [Ah | Ah | Al], B rows =
-// [hi | lo | hi] (the lo lo term, about 2^-16 relative, is dropped). FP32
-// accumulation in TMEM.
+// [Re; Im] <- [[Fr, -Fi], [Fi, Fr]] [Re; Im]. Every FP32 operand x is split
+// into BF16 terms, and the products of the terms are one GEMM over K = 2N per
+// product, FP32 accumulation in TMEM:
+//   3 products (FWR_TRANSFORM_DFT_BF16X3): x = hi + lo (hi = bf16(x), lo =
+//     bf16(x - hi)); hi hi + hi lo + lo hi over K = 6N with A = [Ah | Ah | Al]
+//     and B rows [hi | lo | hi] (lo lo, about 2^-16 relative, dropped);
+//   6 products (FWR_TRANSFORM_DFT_BF16X6): x = hi + mid + lo, each the BF16
+//     rounding of what the previous terms leave; hh + hm + mh + hl + mm + lh
+//     over K = 12N with A = [Ah | Ah | Am | Ah | Am | Al] and B rows
+//     [h | m | h | l | m | h] (the dropped terms are about 2^-24 relative).
+//     Measured against the FP64 oracle it gives the error of the three
+//     products: the tensor core's FP32 accumulation over K sets the error.
 //
 // Per transform, with the chunk's frames f and row (or column) index x:
 //   right product  B rows (f, r) = row r of Z_f        -> D [2N][(f, r)] = (Z_f F)^T
@@ -39,22 +46,26 @@ typedef __nv_bfloat16 bf16;
 // frames per chunk: the chunk's GEMMs have 2^23 / N columns
 __host__ __device__ inline int chunk_frames(int N) { return (1 << 23) / (N * N); }
 
+// K of the GEMMs: 2N per product
+__host__ __device__ inline int gemm_k(int N, int terms) { return 2 * N * terms; }
+
 struct Ws {
-    bf16* Af;  // [2N][6N] forward operand
-    bf16* Ai;  // [2N][6N] inverse operand
-    bf16* B;   // [chunk N][6N]
+    bf16* Af;  // [2N][K] forward operand
+    bf16* Ai;  // [2N][K] inverse operand
+    bf16* B;   // [chunk N][K]
     float* D;  // [2N][chunk N]
 };
 
-Ws carve(int N, void* ws) {
+Ws carve(int N, int terms, void* ws) {
     Ws w;
     uint8_t* p = static_cast<uint8_t*>(ws);
-    const size_t a = size_t(2 * N) * 6 * N * sizeof(bf16);
+    const size_t K = size_t(gemm_k(N, terms));
+    const size_t a = size_t(2 * N) * K * sizeof(bf16);
     const size_t cols = size_t(chunk_frames(N)) * N;
     w.Af = reinterpret_cast<bf16*>(p);
     w.Ai = reinterpret_cast<bf16*>(p + a);
     w.B = reinterpret_cast<bf16*>(p + 2 * a);
-    w.D = reinterpret_cast<float*>(p + 2 * a + cols * 6 * N * sizeof(bf16));
+    w.D = reinterpret_cast<float*>(p + 2 * a + cols * K * sizeof(bf16));
     return w;
 }
 
@@ -62,20 +73,59 @@ __device__ __forceinline__ void split(float x, bf16& hi, bf16& lo) {
     hi = __float2bfloat16_rn(x);
     lo = __float2bfloat16_rn(x - __bfloat162float(hi));
 }
+__device__ __forceinline__ void split3(float x, bf16& hi, bf16& mid, bf16& lo) {
+    hi = __float2bfloat16_rn(x);
+    const float r = x - __bfloat162float(hi);
+    mid = __float2bfloat16_rn(r);
+    lo = __float2bfloat16_rn(r - __bfloat162float(mid));
+}
 
-// entry k of a B row of length 6N: [hi | lo | hi]
-__device__ __forceinline__ void put_split(bf16* row, int N, int k, float x) {
-    bf16 h, l;
-    split(x, h, l);
-    row[k] = h;
-    row[2 * N + k] = l;
-    row[4 * N + k] = h;
+// entry k of a B row: 3 products [hi | lo | hi] (K = 6N); 6 products
+// [h | m | h | l | m | h] (K = 12N)
+__device__ __forceinline__ void put_split(bf16* row, int N, int k, float x, int terms) {
+    if (terms == 3) {
+        bf16 h, l;
+        split(x, h, l);
+        row[k] = h;
+        row[2 * N + k] = l;
+        row[4 * N + k] = h;
+    } else {
+        bf16 h, m, l;
+        split3(x, h, m, l);
+        row[k] = h;
+        row[2 * N + k] = m;
+        row[4 * N + k] = h;
+        row[6 * N + k] = l;
+        row[8 * N + k] = m;
+        row[10 * N + k] = h;
+    }
 }
 
 // A operands from the twiddle table: forward [[Fr, -Fi], [Fi, Fr]], inverse
-// with Fi -> -Fi; rows [Ah | Ah | Al].
-__global__ void k_dg_operands(const float2* tw, int N, bf16* Af, bf16* Ai) {
+// with Fi -> -Fi; rows [Ah | Ah | Al] (3 products) or [Ah | Ah | Am | Ah | Am
+// | Al] (6 products).
+__device__ __forceinline__ void put_a(bf16* row, int N, int c, float v, int terms) {
+    if (terms == 3) {
+        bf16 h, l;
+        split(v, h, l);
+        row[c] = h;
+        row[2 * N + c] = h;
+        row[4 * N + c] = l;
+    } else {
+        bf16 h, m, l;
+        split3(v, h, m, l);
+        row[c] = h;
+        row[2 * N + c] = h;
+        row[4 * N + c] = m;
+        row[6 * N + c] = h;
+        row[8 * N + c] = m;
+        row[10 * N + c] = l;
+    }
+}
+
+__global__ void k_dg_operands(const float2* tw, int N, int terms, bf16* Af, bf16* Ai) {
     const int i = blockIdx.x;  // output row 0 .. 2N
+    const size_t K = size_t(gemm_k(N, terms));
     for (int c = threadIdx.x; c < 2 * N; c += blockDim.x) {
         const int io = i % N, co = c % N;
         const float2 f = tw[(long long)io * co % N];  // (cos, -sin) of 2 pi io co / N
@@ -83,15 +133,8 @@ __global__ void k_dg_operands(const float2* tw, int N, bf16* Af, bf16* Ai) {
         // forward: Re out = Fr Re - Fi Im, Im out = Fi Re + Fr Im (Fi = f.y)
         const float vf = im_out == im_in ? f.x : (im_out ? f.y : -f.y);
         const float vi = im_out == im_in ? f.x : (im_out ? -f.y : f.y);
-        bf16 h, l;
-        split(vf, h, l);
-        Af[(size_t)i * 6 * N + c] = h;
-        Af[(size_t)i * 6 * N + 2 * N + c] = h;
-        Af[(size_t)i * 6 * N + 4 * N + c] = l;
-        split(vi, h, l);
-        Ai[(size_t)i * 6 * N + c] = h;
-        Ai[(size_t)i * 6 * N + 2 * N + c] = h;
-        Ai[(size_t)i * 6 * N + 4 * N + c] = l;
+        put_a(Af + (size_t)i * K, N, c, vf, terms);
+        put_a(Ai + (size_t)i * K, N, c, vi, terms);
     }
 }
 
@@ -102,7 +145,7 @@ __global__ void k_dg_operands(const float2* tw, int N, bf16* Af, bf16* Ai) {
 // threads per row.
 __global__ void k_dg_rows(const float* D, long long ldd, bool embed, const float* slopes, const float* ext,
                           const uint8_t* mask, int n, int off, int N, int f0, bool fill, bf16* B,
-                          unsigned* status) {
+                          unsigned* status, int terms) {
     const int row = blockIdx.x;  // (f, r) in the chunk
     const int fl = row / N, r = row % N, f = f0 + fl;
     const int nn = n * n;
@@ -144,27 +187,27 @@ __global__ void k_dg_rows(const float* D, long long ldd, bool embed, const float
             xs[1] = -s;  // column N - 1 is this thread's second cell
         }
     }
-    bf16* b = B + (size_t)row * 6 * N;
+    bf16* b = B + (size_t)row * gemm_k(N, terms);
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
         const int c = threadIdx.x + u * (N / 2);
-        put_split(b, N, c, xs[u]);
-        put_split(b, N, N + c, ys[u]);
+        put_split(b, N, c, xs[u], terms);
+        put_split(b, N, N + c, ys[u], terms);
     }
 }
 
 // D (rows: output index, real then imaginary; columns (f, x)) -> B rows
 // (f, i) = [Re D[i][(f, .)], Im D[N + i][(f, .)]] split: the next product's
 // operand. One block of N / 2 threads per B row.
-__global__ void k_dg_resplit(const float* D, long long ldd, int N, bf16* B) {
+__global__ void k_dg_resplit(const float* D, long long ldd, int N, bf16* B, int terms) {
     const int row = blockIdx.x;
     const int fl = row / N, i = row % N;
-    bf16* b = B + (size_t)row * 6 * N;
+    bf16* b = B + (size_t)row * gemm_k(N, terms);
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
         const int x = threadIdx.x + u * (N / 2);
-        put_split(b, N, x, D[(size_t)i * ldd + (size_t)fl * N + x]);
-        put_split(b, N, N + x, D[(size_t)(N + i) * ldd + (size_t)fl * N + x]);
+        put_split(b, N, x, D[(size_t)i * ldd + (size_t)fl * N + x], terms);
+        put_split(b, N, N + x, D[(size_t)(N + i) * ldd + (size_t)fl * N + x], terms);
     }
 }
 
@@ -175,11 +218,11 @@ __global__ void k_dg_resplit(const float* D, long long ldd, int N, bf16* B) {
 // N / 2, the rest from (-ky, -kx)) that hold 1/N^2. With `fill`, the y part
 // of Eq. PC: Sy(ky, kx) -= Sy(0, kx) e^{2 i pi ky / N}.
 __global__ void k_dg_spectral(const float* D, long long ldd, int N, const Tables<float> tab, bool final, bool fill,
-                              bf16* B) {
+                              bf16* B, int terms) {
     const int row = blockIdx.x;  // (f, ky)
     const int fl = row / N, ky = row % N, kyn = (N - ky) & (N - 1);
     const float* wt = final ? tab.wfin : tab.iota;
-    bf16* b = B + (size_t)row * 6 * N;
+    bf16* b = B + (size_t)row * gemm_k(N, terms);
     const size_t cb = (size_t)fl * N;
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
@@ -208,8 +251,8 @@ __global__ void k_dg_spectral(const float* D, long long ldd, int N, const Tables
         } else {
             out = ph;
         }
-        put_split(b, N, kx, out.x);
-        put_split(b, N, N + kx, out.y);
+        put_split(b, N, kx, out.x, terms);
+        put_split(b, N, N + kx, out.y, terms);
     }
 }
 
@@ -223,24 +266,25 @@ __global__ void k_dg_phase(const float* D, long long ldd, int N, int f0, int nf,
 
 }  // namespace
 
-size_t dftgemm_ws_bytes(int N) {
-    if (N != 128 && N != 256) return 0;
-    const size_t cols = size_t(chunk_frames(N)) * N;
-    return 2 * size_t(2 * N) * 6 * N * sizeof(bf16) + cols * 6 * N * sizeof(bf16) + size_t(2 * N) * cols * sizeof(float);
+size_t dftgemm_ws_bytes(int N, int terms) {
+    if ((N != 128 && N != 256) || (terms != 3 && terms != 6)) return 0;
+    const size_t cols = size_t(chunk_frames(N)) * N, K = size_t(gemm_k(N, terms));
+    return 2 * size_t(2 * N) * K * sizeof(bf16) + cols * K * sizeof(bf16) + size_t(2 * N) * cols * sizeof(float);
 }
 
 int dftgemm_chunk(int N) { return chunk_frames(N); }
 
-cudaError_t dftgemm_setup(int N, const float2* tw, void* ws) {
-    Ws w = carve(N, ws);
-    k_dg_operands<<<2 * N, 256>>>(tw, N, w.Af, w.Ai);
+cudaError_t dftgemm_setup(int N, int terms, const float2* tw, void* ws) {
+    Ws w = carve(N, terms, ws);
+    k_dg_operands<<<2 * N, 256>>>(tw, N, terms, w.Af, w.Ai);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? cudaDeviceSynchronize() : e;
 }
 
-cudaError_t launch_dftgemm_f32(int N, const Params<float>& p, void* ws, cudaStream_t s) {
-    if ((N != 128 && N != 256) || !ws) return cudaErrorInvalidValue;
-    const Ws w = carve(N, ws);
+cudaError_t launch_dftgemm_f32(int N, int terms, const Params<float>& p, void* ws, cudaStream_t s) {
+    if ((N != 128 && N != 256) || (terms != 3 && terms != 6) || !ws) return cudaErrorInvalidValue;
+    const Ws w = carve(N, terms, ws);
+    const int K = gemm_k(N, terms);
     const int chunk = chunk_frames(N);
     const long long ldd = (long long)chunk * N;
     int* st = reinterpret_cast<int*>(p.status);
@@ -252,26 +296,26 @@ cudaError_t launch_dftgemm_f32(int N, const Params<float>& p, void* ws, cudaStre
             const bool final = it == p.iters;
             const bool fill = p.periodic == PERIODIC_BEFORE_EACH_FFT || (p.periodic == PERIODIC_FINAL_ONLY && final);
             k_dg_rows<<<nf * N, N / 2, 0, s>>>(w.D, ldd, it == 0, p.slopes, p.ext_init, p.mask, p.n, p.off, N, f0,
-                                               fill, w.B, p.status);
+                                               fill, w.B, p.status, terms);
             cudaError_t e = cudaGetLastError();
             // forward transform: right product, re-split, left product
-            if (e == cudaSuccess) e = tc_gemm(w.Af, 2 * N, 6 * N, w.B, cols, w.D, false, ldd, st, s);
+            if (e == cudaSuccess) e = tc_gemm(w.Af, 2 * N, K, w.B, cols, w.D, false, ldd, st, s);
             if (e == cudaSuccess) {
-                k_dg_resplit<<<nf * N, N / 2, 0, s>>>(w.D, ldd, N, w.B);
+                k_dg_resplit<<<nf * N, N / 2, 0, s>>>(w.D, ldd, N, w.B, terms);
                 e = cudaGetLastError();
             }
-            if (e == cudaSuccess) e = tc_gemm(w.Af, 2 * N, 6 * N, w.B, cols, w.D, false, ldd, st, s);
+            if (e == cudaSuccess) e = tc_gemm(w.Af, 2 * N, K, w.B, cols, w.D, false, ldd, st, s);
             if (e == cudaSuccess) {
-                k_dg_spectral<<<nf * N, N / 2, 0, s>>>(w.D, ldd, N, p.tab, final, fill, w.B);
+                k_dg_spectral<<<nf * N, N / 2, 0, s>>>(w.D, ldd, N, p.tab, final, fill, w.B, terms);
                 e = cudaGetLastError();
             }
             // inverse transform
-            if (e == cudaSuccess) e = tc_gemm(w.Ai, 2 * N, 6 * N, w.B, cols, w.D, false, ldd, st, s);
+            if (e == cudaSuccess) e = tc_gemm(w.Ai, 2 * N, K, w.B, cols, w.D, false, ldd, st, s);
             if (e == cudaSuccess) {
-                k_dg_resplit<<<nf * N, N / 2, 0, s>>>(w.D, ldd, N, w.B);
+                k_dg_resplit<<<nf * N, N / 2, 0, s>>>(w.D, ldd, N, w.B, terms);
                 e = cudaGetLastError();
             }
-            if (e == cudaSuccess) e = tc_gemm(w.Ai, 2 * N, 6 * N, w.B, cols, w.D, false, ldd, st, s);
+            if (e == cudaSuccess) e = tc_gemm(w.Ai, 2 * N, K, w.B, cols, w.D, false, ldd, st, s);
             if (e != cudaSuccess) return e;
         }
         if (p.phase) {

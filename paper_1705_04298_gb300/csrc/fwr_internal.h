@@ -134,9 +134,10 @@ cudaError_t tc_gemm(const void* A, int M, int K, const void* B, long long N, voi
 // Batched split-BF16 DFT-as-GEMM path for N = 128 and 256 (fwr_dftgemm_tc.cu):
 // every 2-D transform of Algorithm 1 and of the final reconstruction as two
 // tcgen05 GEMMs over a chunk of frames. Workspace: dftgemm_ws_bytes(N) bytes.
-size_t dftgemm_ws_bytes(int N);
+// terms: 3 or 6 split products (FWR_TRANSFORM_DFT_BF16X3 / X6).
+size_t dftgemm_ws_bytes(int N, int terms);
 int dftgemm_chunk(int N);
-cudaError_t dftgemm_setup(int N, const float2* tw, void* ws);  // fills the DFT operand matrices of ws
-cudaError_t launch_dftgemm_f32(int N, const Params<float>& p, void* ws, cudaStream_t s);
+cudaError_t dftgemm_setup(int N, int terms, const float2* tw, void* ws);  // fills the DFT operand matrices of ws
+cudaError_t launch_dftgemm_f32(int N, int terms, const Params<float>& p, void* ws, cudaStream_t s);
 
 }  // namespace fwr

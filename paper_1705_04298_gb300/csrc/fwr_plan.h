@@ -64,6 +64,7 @@ struct fwr_plan {
     float2* d_static_scratch = nullptr;
     // DFT-as-GEMM transform on 128^2 / 256^2 grids: operands and chunk buffers
     void* d_dftws = nullptr;
+    int dftws_terms = 0;  // split products the workspace was built for (3 or 6)
     int scratch_ctas = 0;
     // host-path staging
     float* d_stage_in = nullptr;

@@ -33,6 +33,7 @@ EXT_ZERO = 0
 EXT_HUDGIN = 1
 TRANSFORM_FFT = 0
 TRANSFORM_DFT_BF16X3 = 1
+TRANSFORM_DFT_BF16X6 = 2
 STATIC_SCRATCH_GRIDS = 16
 NET_OPT_CONV = 1
 NET_CONV_AUTO = 0

@@ -122,3 +122,43 @@ def test_transform_option_limits(fwr):
     assert e.value.code == 2
     with pytest.raises(fwr.FwrError):
         plan.set_transform(7)
+
+
+@pytest.mark.parametrize("n,pad,k,filt,periodic", [(40, 3.2, 10, "wiener", 0), (80, 3.2, 5, "lsq", 0),
+                                                    (128, 2.0, 2, "lsq", 1)])
+def test_six_product_split(fwr, n, pad, k, filt, periodic):
+    """FWR_TRANSFORM_DFT_BF16X6: the three-way BF16 split with six products
+    per real product represents every operand to about 24 bits, yet the
+    measured error against the FP64 oracle is that of the three-product split
+    (1.6e-5 at 128^2, k = 10; 2.1e-5 at 256^2, k = 5): the tensor core's FP32
+    accumulation over K, not the operand split, sets the error of this path.
+    Held to the same bounds as the three-product split."""
+    r0p, L0p = synth.pitch_units(n, 0.15, 25.0)
+    sig = 0.05
+    F = 2
+    sl, _, mask = synth.batch(n, F, 800 + n + k, sig)
+    plan = fwr.Plan(mask, pad, fwr.WIENER if filt == "wiener" else fwr.LSQ, sig ** 2, r0p, L0p)
+    plan.set_periodic(periodic)
+    plan.set_transform(fwr.TRANSFORM_DFT_BF16X6)
+    ph = plan.reconstruct(torch.tensor(sl, dtype=torch.float32, device="cuda"), k).cpu().numpy()
+    assert plan.status() == "FWR_OK"
+    worst = 0.0
+    for f in range(F):
+        ref, _ = oracle.reconstruct(sl[f], mask, pad, k,
+                                    oracle.FILTER_WIENER if filt == "wiener" else oracle.FILTER_LSQ,
+                                    sig ** 2, r0p, L0p, periodic)
+        worst = max(worst, rel_rms(ph[f], ref))
+        assert within(ph[f], ref, DFT_RMS, DFT_MAX, where="X6 N=%d k=%d f=%d" % (plan.N, k, f))
+    print("six-product split N=%d k=%d: relative phase rms %.2e" % (plan.N, k, worst))
+    # back and forth between the product counts keeps a working plan
+    plan.set_transform(fwr.TRANSFORM_DFT_BF16X3)
+    plan.set_transform(fwr.TRANSFORM_DFT_BF16X6)
+    again = plan.reconstruct(torch.tensor(sl, dtype=torch.float32, device="cuda"), k).cpu().numpy()
+    assert np.array_equal(again, ph)
+
+
+def test_six_product_split_limits(fwr):
+    plan = fwr.Plan(synth.pupil_mask(16), 2.0, fwr.LSQ)  # 32^2: per-frame mma.sync path has 3 products only
+    with pytest.raises(fwr.FwrError) as e:
+        plan.set_transform(fwr.TRANSFORM_DFT_BF16X6)
+    assert e.value.code == 2
