@@ -16,17 +16,32 @@ namespace fwr {
 template <typename T, int N, bool HUD>
 __global__ void __launch_bounds__(4 * N)
 fused_kernel(Params<T> p) {
+    // FP32 on 128^2 (one CTA per SM): the LSQ coefficients live in tensor memory
+    constexpr bool TMC = sizeof(T) == 4 && N == 128;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_bad;
+    __shared__ uint32_t s_tmem;
     if (threadIdx.x == 0) s_bad = 0;
+    if constexpr (TMC) {
+        if (threadIdx.x < 32) {
+            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                             uint32_t(__cvta_generic_to_shared(&s_tmem))),
+                         "r"(FUSED_TMEM_COLS)
+                         : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    }
     FusedCtx<T, N> c;
-    fused_setup<T, N>(c, smem, p.tab, p.mask, p.n, p.off, p.periodic, p.wf_smem != 0);
+    fused_setup<T, N, TMC>(c, smem, p.tab, p.mask, p.n, p.off, p.periodic, p.wf_smem != 0, TMC ? s_tmem : 0u);
     const int nn = p.n * p.n;
     bool finite = true;
     for (int f = blockIdx.x; f < p.F; f += gridDim.x) {
         // the CTA's next frame's slopes into L2 while this one is worked
         if (f + int(gridDim.x) < p.F) prefetch_l2(p.slopes + size_t(f + gridDim.x) * 2 * nn, 2 * nn * sizeof(T));
-        finite &= fused_frame<T, N>(c, p.slopes + size_t(f) * 2 * nn,
+        finite &= fused_frame<T, N, TMC>(c, p.slopes + size_t(f) * 2 * nn,
                                     p.ext_init ? p.ext_init + size_t(f) * 2 * N * N : nullptr,
                                     p.ext_init_h ? p.ext_init_h + size_t(f) * 2 * N * N : nullptr,
                                     p.phase ? p.phase + size_t(f) * N * N : nullptr,
@@ -35,8 +50,17 @@ fused_kernel(Params<T> p) {
         __syncthreads();
     }
     if (!finite) atomicOr(&s_bad, 1);
+    if constexpr (TMC) asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
     if (threadIdx.x == 0 && s_bad) atomicOr(p.status, STATUS_NONFINITE);
+    if constexpr (TMC) {
+        if (threadIdx.x < 32) {
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(s_tmem),
+                         "r"(FUSED_TMEM_COLS)
+                         : "memory");
+        }
+    }
 }
 
 // Standalone batched 2-D FFT through the same three passes (test entry):

@@ -145,6 +145,59 @@ __device__ __forceinline__ quad<float> load_pt(const float* p) {
 }
 __device__ __forceinline__ quad<double> load_pt(const double* p) { return {p[0], p[1], p[2], p[3]}; }
 
+__device__ __forceinline__ float mulrn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mulrn(double a, double b) { return __dmul_rn(a, b); }
+
+// LSQ projection of one bin pair (Algorithm 1 step 2, formula of Sec. 3.3)
+// with the separable factors p(u) = a(u) conj T(u), |a(u)|^2, |T(u)|^2 of the
+// bin's column (pux, puy, 2 ha2u = |a(u)|^2, 2 ht2u = |T(u)|^2) and row (pv),
+// and w = 1/|G|^2 / N^2: the projected bin is
+//   Z'(k) = al z(k) + (be + i ga) conj z(-k),
+// al = w (|G|^2/2 + Im P), be = w (|Gx|^2 - |Gy|^2)/2, ga = w Re P, P = p(u)
+// conj p(v). Every operation is written out (no contraction left to the
+// compiler), so the coefficients come out bitwise the same wherever they are
+// computed.
+template <typename T>
+__device__ __forceinline__ void lsq_coefs(T w, T pux, T puy, T ha2u, T ht2u, const quad<T>& pv, T& al, T& be,
+                                          T& ga) {
+    const T Py = fmadd(puy, pv.x, -mulrn(pux, pv.y));
+    const T ca = fmadd(ha2u, pv.w, fmadd(ht2u, pv.z, Py));
+    const T cb = fmadd(ha2u, pv.w, -mulrn(ht2u, pv.z));
+    const T cc = fmadd(pux, pv.x, mulrn(puy, pv.y));
+    al = mulrn(w, ca);
+    be = mulrn(w, cb);
+    ga = mulrn(w, cc);
+}
+template <typename T, typename V>
+__device__ __forceinline__ V lsq_apply(T al, T be, T ga, V z1, V z2) {
+    return mk(fmadd(al, z1.x, fmadd(be, z2.x, mulrn(ga, z2.y))), fmadd(al, z1.y, fmadd(ga, z2.x, -mulrn(be, z2.y))));
+}
+
+// Tensor memory as per-thread storage (32x32b shape: a thread reaches the
+// lane of its warp quarter). Stores of 32 and loads of 8 consecutive columns.
+__device__ __forceinline__ void tm_st32(uint32_t taddr, const float (&v)[32]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+        "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};\n" ::"r"(taddr),
+        "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7]), "f"(v[8]),
+        "f"(v[9]), "f"(v[10]), "f"(v[11]), "f"(v[12]), "f"(v[13]), "f"(v[14]), "f"(v[15]), "f"(v[16]),
+        "f"(v[17]), "f"(v[18]), "f"(v[19]), "f"(v[20]), "f"(v[21]), "f"(v[22]), "f"(v[23]), "f"(v[24]),
+        "f"(v[25]), "f"(v[26]), "f"(v[27]), "f"(v[28]), "f"(v[29]), "f"(v[30]), "f"(v[31])
+        : "memory");
+}
+__device__ __forceinline__ void tm_ld8(uint32_t taddr, float (&v)[8]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+                 : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
+                 : "r"(taddr)
+                 : "memory");
+}
+__device__ __forceinline__ void tm_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
+__device__ __forceinline__ void tm_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory"); }
+
+// Columns of tensor memory the main kernel allocates (the per-thread LSQ
+// coefficients: 3 x 32 per thread, four warps per lane quarter)
+constexpr uint32_t FUSED_TMEM_COLS = 512;
+
 template <bool INV, typename V>
 __device__ __forceinline__ V twiddle(V x, V w) {
     return INV ? cmulc(w, x) : cmul(x, w);
@@ -270,13 +323,17 @@ struct FusedCtx {
     const T* ion;
     const T* wfp;
     const T* wfn;
+    uint32_t tcoef;  // TMC: tensor-memory address of this thread's LSQ coefficients
 };
 
 // Load a plan's tables into shared memory and set the per-thread roles.
 // Called by every thread of the CTA; ends with a barrier.
-template <typename T, int N>
+// TMC (FP32, one CTA per SM): the LSQ coefficients of the thread's 32 bins are
+// computed here once and kept in tensor memory at tmem (the CTA's allocation).
+template <typename T, int N, bool TMC = false>
 __device__ __forceinline__ void fused_setup(FusedCtx<T, N>& c, unsigned char* smem, const Tables<T>& tab,
-                                            const uint8_t* mask, int n, int off, int mode, bool wf_smem = false) {
+                                            const uint8_t* mask, int n, int off, int mode, bool wf_smem = false,
+                                            uint32_t tmem = 0) {
     typedef typename cvec<T>::type V;
     typedef Layout<T, N> L;
     constexpr int R = N / 4, NT = 4 * N, H = N / 2, S = L::S;
@@ -365,8 +422,29 @@ __device__ __forceinline__ void fused_setup(FusedCtx<T, N>& c, unsigned char* sm
     // final weights: the resident copy (storage-column order) or the table in global memory
     c.wfp = wf ? wf + q1 * N + gam : tab.wfin + q1 * N + kx;
     c.wfn = wf ? wf + (N - q1) * N + gamp : tab.wfin + (N - q1) * N + kxn;
+    if constexpr (TMC) {
+        static_assert(sizeof(T) == 4 && N / 4 == 32, "tensor-memory coefficients: FP32, 32 bins per thread");
+        // columns: al at +0, be at +32, ga at +64 (bin q2 at + q2); lane quarter warp mod 4
+        const int warp = tid >> 5;
+        c.tcoef = tmem + (uint32_t(32 * (warp & 3)) << 16) + uint32_t(96 * (warp >> 2));
+        const T ha2u = T(0.5) * c.a2u, ht2u = T(0.5) * c.t2u;
+        // one coefficient at a time (32 live values): al, be, ga
+#pragma unroll 1
+        for (int which = 0; which < 3; ++which) {
+            float v[32];
+#pragma unroll
+            for (int q2 = 0; q2 < R; ++q2) {
+                const bool lo = q2 < R / 2 || (q2 == R / 2 && q1 == 0);
+                const T w = lo ? c.iop[4 * N * q2] : c.ion[-4 * N * q2];
+                T al, be, ga;
+                lsq_coefs(w, c.pux, c.puy, ha2u, ht2u, load_pt(c.ptv + 16 * q2), al, be, ga);
+                v[q2] = which == 0 ? al : (which == 1 ? be : ga);
+            }
+            tm_st32(c.tcoef + uint32_t(32 * which), v);
+            tm_wait_st();
+        }
+    }
     __syncthreads();
-
 }
 
 // One frame through the whole path (embed, iterations, final filter) with
@@ -374,7 +452,7 @@ __device__ __forceinline__ void fused_setup(FusedCtx<T, N>& c, unsigned char* sm
 // warm start or nullptr; phase: [N][N] output or nullptr; ext_out: [2][N][N]
 // extended slopes or nullptr. Called by every thread; returns false in the
 // threads that saw a non-finite measured slope.
-template <typename T, int N>
+template <typename T, int N, bool TMC = false>
 __device__ __forceinline__ bool fused_frame(const FusedCtx<T, N>& c, const T* sl, const T* ext,
                                             const uint16_t* exth, T* phase, T* ext_out, int iters,
                                             const int16_t* hud = nullptr) {
@@ -554,8 +632,17 @@ __device__ __forceinline__ bool fused_frame(const FusedCtx<T, N>& c, const T* sl
         // ---- spectral step on bins ky = q1 + 4 q2, kx
         // partner row of -ky: R q1n + q2n, q2n = R - 1 - q2 (q1 > 0) or R - q2 (q1 = 0, q2 > 0)
         const V* const partq = q1 == 0 ? partp + S : partp;
+        float tal[8], tbe[8], tga[8];  // TMC: this chunk's coefficients
 #pragma unroll
         for (int q2 = 0; q2 < R; ++q2) {
+            if constexpr (TMC) {
+                if (!final && (q2 & 7) == 0) {
+                    tm_ld8(c.tcoef + q2, tal);
+                    tm_ld8(c.tcoef + 32 + q2, tbe);
+                    tm_ld8(c.tcoef + 64 + q2, tga);
+                    tm_wait_ld();
+                }
+            }
             const V z2 = q2 == 0 ? (q1 == 0 ? partp[0] : partp[S * (R - 1)]) : partq[S * (R - 1 - q2)];
             const V z1 = x[q2];
             const V z2c = mk(z2.x, -z2.y);
@@ -564,18 +651,14 @@ __device__ __forceinline__ bool fused_frame(const FusedCtx<T, N>& c, const T* sl
             const bool lo = q2 < R / 2 || (q2 == R / 2 && q1 == 0);
             if (!final) {
                 // Algorithm 1 step 2: LSQ phase, slopes re-synthesised through G
-                const T w = lo ? iop[4 * N * q2] : ion[-4 * N * q2];
-                const auto pv = load_pt(ptv + 16 * q2);
-                const T pvx = pv.x, pvy = pv.y, a2v = pv.z, t2v = pv.w;
-                // alpha = w a, beta = w (b + i c): a = |G|^2/2 + Im P,
-                // b = (|Gx|^2 - |Gy|^2)/2, c = Re P; w scales the combination
-                const T Py = puy * pvx - pux * pvy;
-                const T ca = ha2u * t2v + (ht2u * a2v + Py);
-                const T cb = ha2u * t2v - ht2u * a2v;
-                const T cc = pux * pvx + puy * pvy;
-                const T yx = ca * z1.x + cb * z2c.x - cc * z2c.y;
-                const T yy = ca * z1.y + cb * z2c.y + cc * z2c.x;
-                x[q2] = mk(w * yx, w * yy);
+                if constexpr (TMC) {
+                    x[q2] = lsq_apply(T(tal[q2 & 7]), T(tbe[q2 & 7]), T(tga[q2 & 7]), z1, z2);
+                } else {
+                    const T w = lo ? iop[4 * N * q2] : ion[-4 * N * q2];
+                    T al, be, ga;
+                    lsq_coefs(w, pux, puy, ha2u, ht2u, load_pt(ptv + 16 * q2), al, be, ga);
+                    x[q2] = lsq_apply(al, be, ga, z1, z2);
+                }
             } else {
                 // Eq. 2: phi = Rx Sx + Ry Sy with 2 Sx = z1 + conj z2, 2 Sy = (z1 - conj z2) / i
                 const int ky = q1 + 4 * q2;
