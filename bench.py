@@ -75,9 +75,12 @@ TRAFFIC = {
     "97a3eb880aeb3f5d": 18883840,
     # compile-time spectral selects, slope prefetch, unrolled set-up: 12.982 MB + 5.505 MB
     "b7a334ff342cde75": 18486784,
-    # current kernel (+ the Hudgin-extension instantiation; ncu --metrics dram__bytes_read.sum,
+    # + the Hudgin-extension instantiation (ncu --metrics dram__bytes_read.sum,
     # dram__bytes_write.sum, one k = 10 launch of 1000 frames): 12.98 MB + 4.83 MB
     "da16ea3515ab57b7": 17810000,
+    # LSQ coefficients in tensor memory (ncu --set full, one k = 10 launch of 1000
+    # frames, bench.py --workload fused128): 12.988 MB read + 5.487 MB written
+    "28460c3873c63f98": 18475008,
 }
 
 
