@@ -81,6 +81,10 @@ TRAFFIC = {
     # LSQ coefficients in tensor memory (ncu --set full, one k = 10 launch of 1000
     # frames, bench.py --workload fused128): 12.988 MB read + 5.487 MB written
     "28460c3873c63f98": 18475008,
+    # the same kernel after the slab plans' L2-window fields joined the launch
+    # parameters (ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum, one
+    # k = 10 launch of 1000 frames, bench.py --workload fused128): 12.988 MB + 5.089 MB
+    "6b8bd851c4600f15": 18076928,
 }
 
 
@@ -339,7 +343,8 @@ def extra_measurements(fwr, synth, torch, flush):
     ms = _time_launches(lambda: p4.reconstruct(s4, 10, ph4), flush, 5, torch)
     tf = flops_per_frame(256, 10) * 1000 / (ms / 1e3) / 1e12
     res["128x128_256grid_k10_frozen_flow"] = {"frames_per_s": 1000 / (ms / 1e3), "ms": ms, "tflops": tf,
-                                              "frac": tf / peak, "launch": {"shape": launch4[0], "ctas": launch4[1]}}
+                                              "frac": tf / peak, "launch": {"shape": launch4[0], "ctas": launch4[1],
+                                                                            "l2_persist": p4.l2_persist}}
     # ELT scale: 200x200 lenslets on 512^2 (slab kernel, grid in HBM), k = 10
     sl5, _, m5 = synth.batch(200, 16, 7000, 0.05)
     p5 = fwr.Plan(m5, 2.56, fwr.LSQ)
@@ -350,8 +355,10 @@ def extra_measurements(fwr, synth, torch, flush):
     ms = _time_launches(lambda: p5.reconstruct(s5, 10, ph5), flush, 3, torch)
     tf = flops_per_frame(512, 10) * F5 / (ms / 1e3) / 1e12
     res["200x200_512grid_k10"] = {"frames": F5, "frames_per_s": F5 / (ms / 1e3), "ms": ms, "tflops": tf,
-                                  "frac": tf / peak, "launch": {"shape": launch5[0], "ctas": launch5[1]}}
+                                  "frac": tf / peak, "launch": {"shape": launch5[0], "ctas": launch5[1],
+                                                                "l2_persist": p5.l2_persist}}
     del s5, ph5
+    fwr.l2_persist_reset(torch.cuda.current_device())  # the rest gets the whole L2 again
     # the same frames through the split-BF16 DFT-as-GEMM transform (batched
     # tcgen05 GEMMs): 2 GEMMs per 2-D transform, 2 (k + 1) transforms, each
     # GEMM 2 x (2N) x (6N) x N flop per frame
@@ -553,6 +560,7 @@ def run_workload(args):
       fused128    40x40 lenslets on 128^2, Wiener, --iters iterations
       slab256     128x128 lenslets on 256^2 (frozen-flow frames), LSQ, --iters
       slab512     200x200 lenslets on 512^2 (ELT scale, seeded frames), LSQ, --iters
+                  (both with the persisting L2 window under --l2-persist 1)
       dftgemm256  the same through the split-BF16 DFT-as-GEMM transform
       unet        the warm-start U-Net forward on 40x40 slopes (committed weights)
       linws       the linear warm start (--rank) alone, then with --iters
@@ -575,12 +583,16 @@ def run_workload(args):
         plan = fwr.Plan(mask, 2.0, fwr.LSQ)
         if args.workload == "dftgemm256":
             plan.set_transform(fwr.TRANSFORM_DFT_BF16X3)
+        elif args.l2_persist:
+            plan.set_l2_persist(1)
         s = torch.tensor(sl, dtype=torch.float32, device="cuda").repeat((F + 31) // 32, 1, 1, 1)[:F].contiguous()
         out = torch.empty((F, plan.N, plan.N), device="cuda")
         runs.append(("%s_k%d" % (args.workload, k), lambda: plan.reconstruct(s, k, out)))
     elif args.workload == "slab512":
         sl, _, mask = synth.batch(200, 16, 7000, 0.05)
         plan = fwr.Plan(mask, 2.56, fwr.LSQ)
+        if args.l2_persist:
+            plan.set_l2_persist(1)
         s = torch.tensor(sl, dtype=torch.float32, device="cuda").repeat((F + 15) // 16, 1, 1, 1)[:F].contiguous()
         out = torch.empty((F, plan.N, plan.N), device="cuda")
         runs.append(("slab512_k%d" % k, lambda: plan.reconstruct(s, k, out)))
@@ -631,6 +643,8 @@ def main():
     ap.add_argument("--frames", type=int, default=FRAMES)
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--rank", type=int, default=256, help="rank of the linws workload")
+    ap.add_argument("--l2-persist", type=int, default=0, choices=[0, 1],
+                    help="slab256/slab512: FWR_OPT_L2_PERSIST on the plan")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

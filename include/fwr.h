@@ -159,6 +159,21 @@ typedef enum {
  */
 #define FWR_OPT_SHAPE 6
 #define FWR_OPT_CTAS 7
+/*
+ * FWR_OPT_L2_PERSIST (256x256 and 512x512 plans; FWR_ERR_UNSUPPORTED for
+ * others): 1 marks the plan's working memory (one grid per SM) as persisting
+ * in L2 for the slab kernel's launches (an access-policy window launch
+ * attribute; CUDA-graph capturable), so its lines are not evicted by the
+ * phase output and the slopes. Setting it raises the calling process's
+ * persisting-L2 set-aside (cudaLimitPersistingL2CacheSize, a limit of the
+ * CUDA context, released when the process exits; never lowered) to the
+ * working memory's size or the device's maximum, whichever is smaller; the
+ * persisting lines stay in L2 after the launches until other persisting
+ * data or cudaCtxResetPersistingL2Cache displaces them. 0 (default): no
+ * window. Results are bitwise the same either way; fwr_plan_autotune tries
+ * both for these plans.
+ */
+#define FWR_OPT_L2_PERSIST 8
 
 /*
  * Create a plan for an n x n lenslet array (Sec. 2; Algorithm 1 input).
@@ -268,7 +283,8 @@ fwr_status fwr_reconstruct_host(fwr_plan* plan, const float* slopes_host, int n_
                                 float* phase_host, void* stream);
 
 /*
- * Choose the plan's launch shape (FWR_OPT_SHAPE, FWR_OPT_CTAS) by timing the
+ * Choose the plan's launch shape (FWR_OPT_SHAPE, FWR_OPT_CTAS,
+ * FWR_OPT_L2_PERSIST) by timing the
  * candidates on the caller's data: fwr_reconstruct_ex of n_frames frames
  * (slopes_dev, phase_dev as there) with `iters` iterations, one warm-up and
  * three timed launches per candidate, on `stream` (synchronises it). The
@@ -278,13 +294,23 @@ fwr_status fwr_reconstruct_host(fwr_plan* plan, const float* slopes_host, int n_
  * entry for the same key is applied without timing. Candidates: the shapes
  * the plan's grid has (two for 256x256 and for N <= 128 when the final weights
  * fit shared memory) times the CTA counts {all, 3/4, 1/2 of the SMs} (times
- * the CTAs per SM). Every candidate gives bitwise the same phase.
+ * the CTAs per SM), times the L2 window off and on for 256x256 and 512x512
+ * FFT plans (skipped where the device has no persisting L2). Every candidate
+ * gives bitwise the same phase.
  */
 fwr_status fwr_plan_autotune(fwr_plan* plan, const float* slopes_dev, int n_frames, int iters, float* phase_dev,
                              void* stream, const char* cache_path);
-/* The plan's current FWR_OPT_SHAPE and FWR_OPT_CTAS (-1 for NULL). */
+/* The plan's current FWR_OPT_SHAPE, FWR_OPT_CTAS and FWR_OPT_L2_PERSIST (-1 for NULL). */
 int fwr_plan_shape(const fwr_plan* plan);
 int fwr_plan_ctas(const fwr_plan* plan);
+int fwr_plan_l2_persist(const fwr_plan* plan);
+/*
+ * Return every L2 line that FWR_OPT_L2_PERSIST launches left persisting on
+ * `device` to normal status (cudaCtxResetPersistingL2Cache in that device's
+ * context; the set-aside limit stays). Call with no launch of the plan in
+ * flight when other work should have the whole L2 again.
+ */
+fwr_status fwr_l2_persist_reset(int device);
 
 /* Pre-allocate host-path staging for n_frames frames (and the copy streams). */
 fwr_status fwr_plan_reserve(fwr_plan* plan, int n_frames);

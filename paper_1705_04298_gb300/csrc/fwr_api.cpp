@@ -442,6 +442,39 @@ fwr_status fwr_plan_set_option(fwr_plan* p, int key, double value) {
         p->shape = v;
         return FWR_OK;
     }
+    if (key == FWR_OPT_L2_PERSIST) {
+        const int v = int(value);
+        if (double(v) != value || (v != 0 && v != 1)) return FWR_ERR_ARG;
+        if (v == 1 && !p->d_scratch) return FWR_ERR_UNSUPPORTED;
+        if (v == 0) {
+            p->l2_persist = 0;
+            p->l2_bytes = 0;
+            p->l2_hit = 0.f;
+            return FWR_OK;
+        }
+        int prev = 0;
+        cudaGetDevice(&prev);
+        cudaSetDevice(p->device);
+        int maxp = 0, maxw = 0;
+        size_t cur = 0;
+        cudaError_t e = cudaDeviceGetAttribute(&maxp, cudaDevAttrMaxPersistingL2CacheSize, p->device);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&maxw, cudaDevAttrMaxAccessPolicyWindowSize, p->device);
+        if (e == cudaSuccess) e = cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize);
+        const size_t scratch = size_t(p->scratch_ctas) * fwr::slab_scratch_elems_per_cta(p->N) * sizeof(float2);
+        size_t want = scratch < size_t(maxp) ? scratch : size_t(maxp);
+        // the context's set-aside is only ever raised (other plans may use it)
+        if (e == cudaSuccess && want > cur) e = cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want);
+        size_t lim = 0;
+        if (e == cudaSuccess) e = cudaDeviceGetLimit(&lim, cudaLimitPersistingL2CacheSize);
+        cudaSetDevice(prev);
+        if (e != cudaSuccess) return cuda_fail(e, "persisting L2 set-aside");
+        if (maxp <= 0 || maxw <= 0 || lim == 0) return FWR_ERR_UNSUPPORTED;
+        const size_t win = scratch < size_t(maxw) ? scratch : size_t(maxw);
+        p->l2_persist = 1;
+        p->l2_bytes = win;
+        p->l2_hit = float(double(lim) >= double(win) ? 1.0 : double(lim) / double(win));
+        return FWR_OK;
+    }
     if (key == FWR_OPT_CTAS) {
         const int v = int(value);
         if (double(v) != value || v < 0 || v > 65536) return FWR_ERR_ARG;
@@ -490,6 +523,8 @@ fwr_status fwr_reconstruct_ex(fwr_plan* p, const float* slopes, const float* ext
     k.periodic = p->periodic;
     k.shape = p->shape;
     k.ctas = p->ctas;
+    k.l2_bytes = p->l2_bytes;
+    k.l2_hit = p->l2_hit;
     k.status = p->d_status;
     const bool hudgin = p->extension == FWR_EXT_HUDGIN && !ext_init;
     if (hudgin) {
@@ -595,6 +630,8 @@ fwr_status fwr_reconstruct_f64(fwr_plan* p, const double* slopes, const double* 
     k.periodic = p->periodic;
     k.shape = p->shape;
     k.ctas = p->ctas;
+    k.l2_bytes = p->l2_bytes;
+    k.l2_hit = p->l2_hit;
     k.status = p->d_status;
     if (p->extension == FWR_EXT_HUDGIN && !ext_init) {
         if (!pow2(p->N) || !fwr::fused_supported(p->N, 8, p->n)) return FWR_ERR_UNSUPPORTED;
@@ -789,6 +826,8 @@ cudaError_t fwr::launch_warm_bf16(fwr_plan* p, const float* slopes, const uint16
     k.periodic = p->periodic;
     k.shape = p->shape;
     k.ctas = p->ctas;
+    k.l2_bytes = p->l2_bytes;
+    k.l2_hit = p->l2_hit;
     k.status = p->d_status;
     return fwr::launch_fused_f32(p->N, k, s);
 }

@@ -45,6 +45,10 @@ template <typename T> struct Params {
     // read from L2 (0: 1)
     int shape = 0;
     int ctas = 0;   // persistent CTAs (0: every SM, times the resident CTAs per SM)
+    // slab kernel: an L2 access-policy window over the scratch (FWR_OPT_L2_PERSIST),
+    // persisting hits for l2_hit of its l2_bytes; l2_bytes = 0: none
+    size_t l2_bytes = 0;
+    float l2_hit = 0.f;
 };
 
 // Where Eq. PC is applied (same values as FWR_PERIODIC_* in fwr.h).

@@ -47,6 +47,9 @@ struct fwr_plan {
     int g_model = FWR_G_AVERAGED;   // measurement model of the filter tables
     int extension = FWR_EXT_ZERO;   // initial extension without a warm start
     int shape = 0;                  // kernel shape (FWR_OPT_SHAPE)
+    int l2_persist = 0;             // FWR_OPT_L2_PERSIST
+    size_t l2_bytes = 0;            // its access-policy window over d_scratch
+    float l2_hit = 0.f;
     int ctas = 0;                   // persistent CTAs (FWR_OPT_CTAS; 0 = every SM)
     int16_t* d_hud = nullptr;       // [4][n]: pupil edges per column and row (Hudgin extension)
     double pixel = 0.0;             // d_px / d of the filter tables

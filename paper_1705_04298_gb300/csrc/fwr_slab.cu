@@ -67,8 +67,26 @@ cudaError_t launch_slab(int N, const Params<float>& p, float2* scratch, int max_
     if (p.ctas > 0 && p.ctas < grid) grid = p.ctas;
     if (grid > p.F) grid = p.F;
     if (grid < 1) return cudaErrorInvalidConfiguration;
-    kern<<<grid, SNT, slab_smem_bytes(N, p.n), s>>>(p, scratch);
-    return cudaGetLastError();
+    if (p.l2_bytes == 0) {
+        kern<<<grid, SNT, slab_smem_bytes(N, p.n), s>>>(p, scratch);
+        return cudaGetLastError();
+    }
+    // the scratch's lines persist in L2 (the context's set-aside holds them)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(SNT);
+    cfg.dynamicSmemBytes = slab_smem_bytes(N, p.n);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeAccessPolicyWindow;
+    attr[0].val.accessPolicyWindow.base_ptr = scratch;
+    attr[0].val.accessPolicyWindow.num_bytes = p.l2_bytes;
+    attr[0].val.accessPolicyWindow.hitRatio = p.l2_hit;
+    attr[0].val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+    attr[0].val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, p, scratch);
 }
 
 // ---------------------------------------------------------------------------

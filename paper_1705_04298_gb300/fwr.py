@@ -29,6 +29,7 @@ G_FRIED = 1
 OPT_EXTENSION = 5
 OPT_SHAPE = 6
 OPT_CTAS = 7
+OPT_L2_PERSIST = 8
 EXT_ZERO = 0
 EXT_HUDGIN = 1
 TRANSFORM_FFT = 0
@@ -62,6 +63,8 @@ SIGNATURES = {
     "fwr_plan_autotune": (_I, [_P, _P, _I, _I, _P, _P, ctypes.c_char_p]),
     "fwr_plan_shape": (_I, [_P]),
     "fwr_plan_ctas": (_I, [_P]),
+    "fwr_plan_l2_persist": (_I, [_P]),
+    "fwr_l2_persist_reset": (_I, [_I]),
     "fwr_batch_shape": (_I, [_P]),
     "fwr_batch_set_shape": (_I, [_P, _I]),
     "fwr_fft2": (_I, [_I, _P, _P, _I, _I, _P]),
@@ -204,6 +207,11 @@ class Plan:
         """Launch shape (FWR_OPT_SHAPE, 0..2; bitwise the same result)."""
         _check(self._lib.fwr_plan_set_option(self._h, OPT_SHAPE, float(shape)), "fwr_plan_set_option")
 
+    def set_l2_persist(self, on):
+        """FWR_OPT_L2_PERSIST: keep the slab kernel's working memory persisting in
+        L2 (256^2 / 512^2 plans; raises the process's persisting-L2 set-aside)."""
+        _check(self._lib.fwr_plan_set_option(self._h, OPT_L2_PERSIST, float(bool(on))), "fwr_plan_set_option")
+
     def set_ctas(self, ctas):
         """Persistent CTAs of a launch (FWR_OPT_CTAS; 0 = every SM)."""
         _check(self._lib.fwr_plan_set_option(self._h, OPT_CTAS, float(ctas)), "fwr_plan_set_option")
@@ -215,6 +223,10 @@ class Plan:
     @property
     def ctas(self):
         return self._lib.fwr_plan_ctas(self._h)
+
+    @property
+    def l2_persist(self):
+        return self._lib.fwr_plan_l2_persist(self._h)
 
     def autotune(self, slopes, iters, phase, cache_path=None, stream=None):
         """Time the launch shapes on these frames and keep the fastest
@@ -572,6 +584,12 @@ class LinearWarmStart:
             self.close()
         except Exception:
             pass
+
+
+def l2_persist_reset(device=0):
+    """Return the L2 lines that FWR_OPT_L2_PERSIST launches left persisting to
+    normal status (fwr_l2_persist_reset)."""
+    _check(load().fwr_l2_persist_reset(int(device)), "fwr_l2_persist_reset")
 
 
 def fp32_fma_peak(stream=None):

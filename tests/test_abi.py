@@ -87,7 +87,8 @@ def test_python_constants_match_the_header():
         "G_FRIED": fwr.G_FRIED, "EXT_ZERO": fwr.EXT_ZERO, "EXT_HUDGIN": fwr.EXT_HUDGIN,
         "PERIODIC_BEFORE_EACH_FFT": fwr.PERIODIC_BEFORE_EACH_FFT, "PERIODIC_FINAL_ONLY": fwr.PERIODIC_FINAL_ONLY,
         "PERIODIC_NONE": fwr.PERIODIC_NONE, "TRANSFORM_FFT": fwr.TRANSFORM_FFT,
-        "TRANSFORM_DFT_BF16X3": fwr.TRANSFORM_DFT_BF16X3,
+        "TRANSFORM_DFT_BF16X3": fwr.TRANSFORM_DFT_BF16X3, "TRANSFORM_DFT_BF16X6": fwr.TRANSFORM_DFT_BF16X6,
+        "OPT_SHAPE": fwr.OPT_SHAPE, "OPT_CTAS": fwr.OPT_CTAS, "OPT_L2_PERSIST": fwr.OPT_L2_PERSIST,
     }
     for name, value in mirrored.items():
         assert defines.get(name) == value, name

@@ -1,5 +1,6 @@
-"""Launch-shape tuning (fwr_plan_autotune, FWR_OPT_SHAPE, FWR_OPT_CTAS and
-the batch's shape): every candidate shape and persistent-grid size gives
+"""Launch-shape tuning (fwr_plan_autotune, FWR_OPT_SHAPE, FWR_OPT_CTAS,
+FWR_OPT_L2_PERSIST and the batch's shape): every candidate shape,
+persistent-grid size and L2 window gives
 bitwise the phase of the default launch (each frame's arithmetic is fixed;
 only the layout of the work on the GPU changes), the tuner records its
 choice in the cache and a second plan with the same key takes it from
@@ -57,11 +58,54 @@ def test_autotune_records_and_reuses(fwr, tmp_path):
     assert len(lines) == 1
     e = json.loads(lines[0])
     assert (e["shape"], e["ctas"]) == (shape, ctas) and shape in (1, 2)
+    assert e["l2_persist"] in (0, 1) and plan.l2_persist == e["l2_persist"]
     assert "drv" in e["key"] and "|N256" in e["key"]
     assert torch.equal(plan.reconstruct(s, k), ref)
     other = fwr.Plan(mask, 3.2, fwr.LSQ)
     assert other.autotune(s, k, out, cache) == (shape, ctas)
+    assert other.l2_persist == e["l2_persist"]
     assert len(cache.read_text().strip().splitlines()) == 1  # from the cache, not re-timed
+
+
+@pytest.mark.parametrize("n,pad,k", [(80, 3.2, 3), (160, 3.2, 2)])
+def test_l2_window_is_bitwise_the_default(fwr, n, pad, k):
+    """FWR_OPT_L2_PERSIST on the 256^2 and 512^2 slab plans: the same phase,
+    bit for bit, with and without the persisting window, in both shapes."""
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    F = sms + 9
+    sl, _, mask = synth.batch(n, 4, 3200 + n, 0.05)
+    s = torch.tensor(sl, dtype=torch.float32, device="cuda").repeat(F // 4 + 1, 1, 1, 1)[:F].contiguous()
+    plan = fwr.Plan(mask, pad, fwr.LSQ)
+    assert plan.l2_persist == 0
+    ref = plan.reconstruct(s, k).clone()
+    plan.set_l2_persist(1)
+    assert plan.l2_persist == 1
+    for shape in ((0, 1, 2) if plan.N == 256 else (0,)):
+        plan.set_shape(shape)
+        out = plan.reconstruct(s, k)
+        torch.cuda.synchronize()
+        assert torch.equal(out, ref), (plan.N, shape)
+    plan.set_l2_persist(0)
+    assert plan.l2_persist == 0
+    assert torch.equal(plan.reconstruct(s, k), ref)
+    fwr.l2_persist_reset(torch.cuda.current_device())
+    assert torch.equal(plan.reconstruct(s, k), ref)
+    assert plan.status() == "FWR_OK"
+
+
+def test_l2_window_refused_without_slab_memory(fwr):
+    """Grids of 128^2 and below run without working memory in global memory:
+    the window is refused (FWR_ERR_UNSUPPORTED), and a value other than 0 or 1
+    is an argument error; the plan still works afterwards."""
+    plan = fwr.Plan(synth.pupil_mask(40), 3.2, fwr.LSQ)
+    with pytest.raises(fwr.FwrError):
+        plan.set_l2_persist(1)
+    assert plan.l2_persist == 0
+    big = fwr.Plan(synth.pupil_mask(80), 3.2, fwr.LSQ)
+    lib = fwr.load()
+    assert lib.fwr_plan_set_option(big._h, fwr.OPT_L2_PERSIST, 2.0) == 1
+    assert lib.fwr_plan_set_option(big._h, fwr.OPT_L2_PERSIST, 0.5) == 1
+    assert big.l2_persist == 0
 
 
 def test_batch_shapes_bitwise(fwr):
