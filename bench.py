@@ -85,6 +85,9 @@ TRAFFIC = {
     # parameters (ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum, one
     # k = 10 launch of 1000 frames, bench.py --workload fused128): 12.988 MB + 5.089 MB
     "6b8bd851c4600f15": 18076928,
+    # the final filter's bins in a loop of their own (ncu --set full, one k = 10
+    # launch of 1000 frames, bench.py --workload fused128): 13.629 MB + 7.559 MB
+    "c13607d075322aea": 21188608,
 }
 
 
@@ -358,7 +361,6 @@ def extra_measurements(fwr, synth, torch, flush):
                                   "frac": tf / peak, "launch": {"shape": launch5[0], "ctas": launch5[1],
                                                                 "l2_persist": p5.l2_persist}}
     del s5, ph5
-    fwr.l2_persist_reset(torch.cuda.current_device())  # the rest gets the whole L2 again
     # the same frames through the split-BF16 DFT-as-GEMM transform (batched
     # tcgen05 GEMMs): 2 GEMMs per 2-D transform, 2 (k + 1) transforms, each
     # GEMM 2 x (2N) x (6N) x N flop per frame
@@ -394,6 +396,26 @@ def measured_bf16_peak():
             return float(json.load(fh)["bf16_tflops"]), "measured"
     except (OSError, ValueError, KeyError):
         return 1900.0, "fallback"
+
+
+def l2_window_measurement(fwr, synth, torch, flush):
+    """The 256^2 frozen-flow workload of the extras (128x128 lenslets, LSQ,
+    k = 10, 1000 frames, L2 flushed) with FWR_OPT_L2_PERSIST: the slab kernel's
+    working memory held in a persisting L2 window; the set-aside is given back
+    afterwards (fwr_l2_persist_reset)."""
+    peak, _ = fwr.fp32_fma_peak()
+    sl4, _, m4 = synth.frozen_flow(128, 32, 7, 0.05, r0=0.12, L0=25.0)
+    p4 = fwr.Plan(m4, 2.0, fwr.LSQ)
+    s4 = torch.tensor(sl4, dtype=torch.float32, device="cuda").repeat(32, 1, 1, 1)[:1000].contiguous()
+    ph4 = torch.empty((1000, 256, 256), device="cuda")
+    launch = p4.autotune(s4, 10, ph4, os.path.join(OUT_DIR, "fwr_plan_tune.jsonl"))
+    p4.set_l2_persist(1)
+    p4.reconstruct(s4, 10, ph4)
+    ms = _time_launches(lambda: p4.reconstruct(s4, 10, ph4), flush, 5, torch)
+    fwr.l2_persist_reset(torch.cuda.current_device())
+    tf = flops_per_frame(256, 10) * 1000 / (ms / 1e3) / 1e12
+    return {"frames_per_s": 1000 / (ms / 1e3), "ms": ms, "tflops": tf, "frac": tf / peak,
+            "launch": {"shape": launch[0], "ctas": launch[1], "l2_persist": 1}}
 
 
 def learned_measurements(fwr, torch, flush):
@@ -731,6 +753,8 @@ def main():
     if rank == 0 and not args.no_extras:
         extras = extra_measurements(fwr, synth, torch, flush)
         extras["learned_warm_start_40x40_128grid"] = learned_measurements(fwr, torch, flush)
+        # last, since its L2 set-aside would slow what runs after it
+        extras["128x128_256grid_k10_frozen_flow_l2_window"] = l2_window_measurement(fwr, synth, torch, flush)
 
     if rank == 0:
         fl = flops_per_frame(N, k) * FRAMES

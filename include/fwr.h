@@ -169,9 +169,11 @@ typedef enum {
  * CUDA context, released when the process exits; never lowered) to the
  * working memory's size or the device's maximum, whichever is smaller; the
  * persisting lines stay in L2 after the launches until other persisting
- * data or cudaCtxResetPersistingL2Cache displaces them. 0 (default): no
- * window. Results are bitwise the same either way; fwr_plan_autotune tries
- * both for these plans.
+ * data displaces them or fwr_l2_persist_reset is called. The set-aside also
+ * takes L2 from the process's other kernels: measured on the GB300, split-BF16
+ * DFT and warm-start GEMMs run after a windowed 256x256 plan were 25-40 %
+ * slower until the reset. 0 (default): no window. Results are bitwise the
+ * same either way. Opt-in only: fwr_plan_autotune keeps the caller's setting.
  */
 #define FWR_OPT_L2_PERSIST 8
 
@@ -283,8 +285,7 @@ fwr_status fwr_reconstruct_host(fwr_plan* plan, const float* slopes_host, int n_
                                 float* phase_host, void* stream);
 
 /*
- * Choose the plan's launch shape (FWR_OPT_SHAPE, FWR_OPT_CTAS,
- * FWR_OPT_L2_PERSIST) by timing the
+ * Choose the plan's launch shape (FWR_OPT_SHAPE, FWR_OPT_CTAS) by timing the
  * candidates on the caller's data: fwr_reconstruct_ex of n_frames frames
  * (slopes_dev, phase_dev as there) with `iters` iterations, one warm-up and
  * three timed launches per candidate, on `stream` (synchronises it). The
@@ -294,9 +295,9 @@ fwr_status fwr_reconstruct_host(fwr_plan* plan, const float* slopes_host, int n_
  * entry for the same key is applied without timing. Candidates: the shapes
  * the plan's grid has (two for 256x256 and for N <= 128 when the final weights
  * fit shared memory) times the CTA counts {all, 3/4, 1/2 of the SMs} (times
- * the CTAs per SM), times the L2 window off and on for 256x256 and 512x512
- * FFT plans (skipped where the device has no persisting L2). Every candidate
- * gives bitwise the same phase.
+ * the CTAs per SM). FWR_OPT_L2_PERSIST is not a candidate (it stays as
+ * set); a cached entry's value is applied. Every candidate gives bitwise the
+ * same phase.
  */
 fwr_status fwr_plan_autotune(fwr_plan* plan, const float* slopes_dev, int n_frames, int iters, float* phase_dev,
                              void* stream, const char* cache_path);
@@ -305,10 +306,13 @@ int fwr_plan_shape(const fwr_plan* plan);
 int fwr_plan_ctas(const fwr_plan* plan);
 int fwr_plan_l2_persist(const fwr_plan* plan);
 /*
- * Return every L2 line that FWR_OPT_L2_PERSIST launches left persisting on
- * `device` to normal status (cudaCtxResetPersistingL2Cache in that device's
- * context; the set-aside limit stays). Call with no launch of the plan in
- * flight when other work should have the whole L2 again.
+ * Give the whole L2 of `device` back to the process's other work: every line
+ * that FWR_OPT_L2_PERSIST launches left persisting returns to normal status
+ * (cudaCtxResetPersistingL2Cache in that device's context) and the
+ * persisting set-aside returns to its value before the library first raised
+ * it. Plans keep their window option; setting FWR_OPT_L2_PERSIST to 1 again
+ * raises the set-aside again. Call with no launch in flight on the device.
+ * FWR_ERR_ARG for an invalid device.
  */
 fwr_status fwr_l2_persist_reset(int device);
 

@@ -31,6 +31,25 @@ fwr_status fwr::cuda_fail(cudaError_t e, const char* where) {
 void fwr::set_last_error(const char* msg) { std::snprintf(g_last_error, sizeof(g_last_error), "%s", msg); }
 
 namespace {
+std::mutex g_setaside_mu;
+std::map<int, size_t> g_setaside_before;  // device -> set-aside before the first raise
+}  // namespace
+
+void fwr::l2_setaside_note(int device, size_t before) {
+    std::lock_guard<std::mutex> lock(g_setaside_mu);
+    g_setaside_before.emplace(device, before);  // keeps the first value
+}
+
+bool fwr::l2_setaside_before(int device, size_t* before) {
+    std::lock_guard<std::mutex> lock(g_setaside_mu);
+    const auto it = g_setaside_before.find(device);
+    if (it == g_setaside_before.end()) return false;
+    *before = it->second;
+    g_setaside_before.erase(it);
+    return true;
+}
+
+namespace {
 using fwr::cuda_fail;
 
 const double kPi = 3.14159265358979323846;
@@ -462,8 +481,12 @@ fwr_status fwr_plan_set_option(fwr_plan* p, int key, double value) {
         if (e == cudaSuccess) e = cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize);
         const size_t scratch = size_t(p->scratch_ctas) * fwr::slab_scratch_elems_per_cta(p->N) * sizeof(float2);
         size_t want = scratch < size_t(maxp) ? scratch : size_t(maxp);
-        // the context's set-aside is only ever raised (other plans may use it)
-        if (e == cudaSuccess && want > cur) e = cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want);
+        // the context's set-aside is only raised here (other plans may use it);
+        // fwr_l2_persist_reset puts back the value found before the first raise
+        if (e == cudaSuccess && want > cur) {
+            fwr::l2_setaside_note(p->device, cur);
+            e = cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want);
+        }
         size_t lim = 0;
         if (e == cudaSuccess) e = cudaDeviceGetLimit(&lim, cudaLimitPersistingL2CacheSize);
         cudaSetDevice(prev);

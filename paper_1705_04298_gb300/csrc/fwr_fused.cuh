@@ -632,24 +632,25 @@ __device__ __forceinline__ bool fused_frame(const FusedCtx<T, N>& c, const T* sl
         // ---- spectral step on bins ky = q1 + 4 q2, kx
         // partner row of -ky: R q1n + q2n, q2n = R - 1 - q2 (q1 > 0) or R - q2 (q1 = 0, q2 > 0)
         const V* const partq = q1 == 0 ? partp + S : partp;
-        float tal[8], tbe[8], tga[8];  // TMC: this chunk's coefficients
+        // the iterations' projection and the once-per-frame final filter in
+        // loops of their own: interleaved per bin, the final filter's code sat
+        // inside the iteration's path and overflowed the instruction cache
+        // (10 % of the launch time at 128^2)
+        if (!final) {
+            float tal[8], tbe[8], tga[8];  // TMC: this chunk's coefficients
 #pragma unroll
-        for (int q2 = 0; q2 < R; ++q2) {
-            if constexpr (TMC) {
-                if (!final && (q2 & 7) == 0) {
-                    tm_ld8(c.tcoef + q2, tal);
-                    tm_ld8(c.tcoef + 32 + q2, tbe);
-                    tm_ld8(c.tcoef + 64 + q2, tga);
-                    tm_wait_ld();
+            for (int q2 = 0; q2 < R; ++q2) {
+                if constexpr (TMC) {
+                    if ((q2 & 7) == 0) {
+                        tm_ld8(c.tcoef + q2, tal);
+                        tm_ld8(c.tcoef + 32 + q2, tbe);
+                        tm_ld8(c.tcoef + 64 + q2, tga);
+                        tm_wait_ld();
+                    }
                 }
-            }
-            const V z2 = q2 == 0 ? (q1 == 0 ? partp[0] : partp[S * (R - 1)]) : partq[S * (R - 1 - q2)];
-            const V z1 = x[q2];
-            const V z2c = mk(z2.x, -z2.y);
-            // ky = 4 q2 + q1 <= N/2: weight stored at (ky, kx); known at compile
-            // time except for q2 = N/8
-            const bool lo = q2 < R / 2 || (q2 == R / 2 && q1 == 0);
-            if (!final) {
+                const V z2 = q2 == 0 ? (q1 == 0 ? partp[0] : partp[S * (R - 1)]) : partq[S * (R - 1 - q2)];
+                const V z1 = x[q2];
+                const bool lo = q2 < R / 2 || (q2 == R / 2 && q1 == 0);
                 // Algorithm 1 step 2: LSQ phase, slopes re-synthesised through G
                 if constexpr (TMC) {
                     x[q2] = lsq_apply(T(tal[q2 & 7]), T(tbe[q2 & 7]), T(tga[q2 & 7]), z1, z2);
@@ -659,7 +660,16 @@ __device__ __forceinline__ bool fused_frame(const FusedCtx<T, N>& c, const T* sl
                     lsq_coefs(w, pux, puy, ha2u, ht2u, load_pt(ptv + 16 * q2), al, be, ga);
                     x[q2] = lsq_apply(al, be, ga, z1, z2);
                 }
-            } else {
+            }
+        } else {
+#pragma unroll
+            for (int q2 = 0; q2 < R; ++q2) {
+                const V z2 = q2 == 0 ? (q1 == 0 ? partp[0] : partp[S * (R - 1)]) : partq[S * (R - 1 - q2)];
+                const V z1 = x[q2];
+                const V z2c = mk(z2.x, -z2.y);
+                // ky = 4 q2 + q1 <= N/2: weight stored at (ky, kx); known at
+                // compile time except for q2 = N/8
+                const bool lo = q2 < R / 2 || (q2 == R / 2 && q1 == 0);
                 // Eq. 2: phi = Rx Sx + Ry Sy with 2 Sx = z1 + conj z2, 2 Sy = (z1 - conj z2) / i
                 const int ky = q1 + 4 * q2;
                 const V sx = cadd(z1, z2c);

@@ -27,6 +27,10 @@ template <typename T> struct DevTables {
 fwr_status cuda_fail(cudaError_t e, const char* where);
 // Record a message as the thread's last error.
 void set_last_error(const char* msg);
+// The persisting-L2 set-aside of a device before the library first raised it
+// (FWR_OPT_L2_PERSIST): note records it once; before returns false if never raised.
+void l2_setaside_note(int device, size_t before);
+bool l2_setaside_before(int device, size_t* before);
 
 }  // namespace fwr
 

@@ -1,5 +1,5 @@
 // Launch-shape tuning of a plan (fwr_plan_autotune, include/fwr.h): times the
-// kernel shapes, persistent-grid sizes and (256^2, 512^2) L2 windows a plan's grid offers on the
+// kernel shapes and persistent-grid sizes a plan's grid offers on the
 // caller's data and keeps the fastest, with a JSON-lines cache keyed by the
 // device, the driver and runtime versions and the problem. The candidates
 // differ only in how the work is laid out on the GPU; every one gives
@@ -73,7 +73,10 @@ fwr_status fwr_l2_persist_reset(int device) {
     int prev = 0;
     cudaGetDevice(&prev);
     cudaSetDevice(device);
-    const cudaError_t e = cudaCtxResetPersistingL2Cache();
+    cudaError_t e = cudaCtxResetPersistingL2Cache();
+    size_t before = 0;
+    if (e == cudaSuccess && fwr::l2_setaside_before(device, &before))
+        e = cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, before);
     cudaSetDevice(prev);
     return e == cudaSuccess ? FWR_OK : fwr::cuda_fail(e, "fwr_l2_persist_reset");
 }
@@ -103,9 +106,10 @@ fwr_status fwr_plan_autotune(fwr_plan* p, const float* slopes, int n_frames, int
     const bool fft = p->transform == FWR_TRANSFORM_FFT;
     if (fft && p->N == 256) shapes = {2, 1};
     else if (fft && (p->N & (p->N - 1)) == 0 && p->N <= 128) shapes = {1, 2};
-    // the L2 window over the slab kernel's working memory: off and on
+    // the plan's L2 window (FWR_OPT_L2_PERSIST) stays as the caller set it:
+    // its set-aside changes the L2 for everything else the process runs, which
+    // timing the plan alone cannot weigh
     std::vector<int> persist_opts = {p->l2_persist};
-    if (fft && p->N >= 256 && p->d_scratch) persist_opts = {0, 1};
     std::vector<int> ctas_opts = {0};
     if (sms >= 8) {
         ctas_opts.push_back(3 * sms / 4);

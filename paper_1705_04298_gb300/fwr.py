@@ -587,8 +587,9 @@ class LinearWarmStart:
 
 
 def l2_persist_reset(device=0):
-    """Return the L2 lines that FWR_OPT_L2_PERSIST launches left persisting to
-    normal status (fwr_l2_persist_reset)."""
+    """Give the whole L2 back to other work: lines that FWR_OPT_L2_PERSIST
+    launches left persisting return to normal, and the persisting set-aside to
+    its value before the library raised it (fwr_l2_persist_reset)."""
     _check(load().fwr_l2_persist_reset(int(device)), "fwr_l2_persist_reset")
 
 
