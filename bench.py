@@ -88,6 +88,9 @@ TRAFFIC = {
     # the final filter's bins in a loop of their own (ncu --set full, one k = 10
     # launch of 1000 frames, bench.py --workload fused128): 13.629 MB + 7.559 MB
     "c13607d075322aea": 21188608,
+    # the same kernel with a griddepcontrol.wait after its set-up (ncu --metrics
+    # dram__bytes_read.sum,dram__bytes_write.sum, bench.py --workload fused128): 13.648 MB + 6.718 MB
+    "eb5006958f98e602": 20365824,
 }
 
 

@@ -833,7 +833,7 @@ const char* fwr_last_error(void) { return g_last_error; }
 }  // extern "C"
 
 cudaError_t fwr::launch_warm_bf16(fwr_plan* p, const float* slopes, const uint16_t* ext_init_h, int n_frames,
-                                  int iters, float* phase, cudaStream_t s) {
+                                  int iters, float* phase, cudaStream_t s, bool pdl) {
     if (p->transform != FWR_TRANSFORM_FFT || p->N >= 256 || !fwr::fused_supported(p->N, 4, p->n))
         return cudaErrorNotSupported;
     fwr::Params<float> k;
@@ -849,8 +849,7 @@ cudaError_t fwr::launch_warm_bf16(fwr_plan* p, const float* slopes, const uint16
     k.periodic = p->periodic;
     k.shape = p->shape;
     k.ctas = p->ctas;
-    k.l2_bytes = p->l2_bytes;
-    k.l2_hit = p->l2_hit;
     k.status = p->d_status;
+    k.pdl = pdl ? 1 : 0;
     return fwr::launch_fused_f32(p->N, k, s);
 }

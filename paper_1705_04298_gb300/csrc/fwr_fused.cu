@@ -36,6 +36,9 @@ fused_kernel(Params<T> p) {
     }
     FusedCtx<T, N> c;
     fused_setup<T, N, TMC>(c, smem, p.tab, p.mask, p.n, p.off, p.periodic, p.wf_smem != 0, TMC ? s_tmem : 0u);
+    // launched as a dependent (Params::pdl): the set-up above used only the
+    // plan's tables; the frames' inputs are read after the producer completes
+    pdl_wait();
     const int nn = p.n * p.n;
     bool finite = true;
     for (int f = blockIdx.x; f < p.F; f += gridDim.x) {
@@ -167,8 +170,21 @@ cudaError_t launch_n(const Params<T>& p0, cudaStream_t s) {
     int grid = sms * per_sm;
     if (p.ctas > 0 && p.ctas < grid) grid = p.ctas;
     if (grid > p.F) grid = p.F;
-    kern<<<grid, 4 * N, smem, s>>>(p);
-    return cudaGetLastError();
+    if (!p.pdl) {
+        kern<<<grid, 4 * N, smem, s>>>(p);
+        return cudaGetLastError();
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(4 * N);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, p);
 }
 
 size_t fused_bytes(int N, int elem_bytes, int n) {

@@ -49,7 +49,18 @@ template <typename T> struct Params {
     // persisting hits for l2_hit of its l2_bytes; l2_bytes = 0: none
     size_t l2_bytes = 0;
     float l2_hit = 0.f;
+    // fused kernel: launched as a programmatic dependent of the kernel before
+    // it on the stream (its table set-up overlaps that kernel's tail; frames
+    // start after it completes). Only for launches whose stream predecessor is
+    // the library's own producer of this launch's inputs.
+    int pdl = 0;
 };
+
+// Programmatic dependent launch (sm_90+): wait for the grids this one depends
+// on to complete and their writes to be visible (no-op without a dependency);
+// allow the dependent grid to launch once every CTA of this grid has signalled.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
 
 // Where Eq. PC is applied (same values as FWR_PERIODIC_* in fwr.h).
 enum : int { PERIODIC_BEFORE_EACH_FFT = 0, PERIODIC_FINAL_ONLY = 1, PERIODIC_NONE = 2 };

@@ -92,10 +92,12 @@ int device_sms(int device) {
 
 // D = A B^T. mb128 / mb256: B with boxes of 128 / 256 rows. 256-wide tiles
 // when N allows them and they still give every SM a tile, else 128-wide.
+// pdl: launched as a programmatic dependent of the previous kernel on the
+// stream (only where that kernel is the library's producer of A).
 template <typename OutT>
 cudaError_t launch_gemm(const CUtensorMap& ma, const CUtensorMap& mb128, const CUtensorMap& mb256, int M,
                         long long N, int K, OutT* D, long long ldd, int* status, cudaStream_t s,
-                        long long wait_limit = fwr::umma::WAIT_LIMIT) {
+                        long long wait_limit = fwr::umma::WAIT_LIMIT, bool pdl = false) {
     int dev = 0;
     cudaGetDevice(&dev);
     const int sms = device_sms(dev);
@@ -104,15 +106,24 @@ cudaError_t launch_gemm(const CUtensorMap& ma, const CUtensorMap& mb128, const C
     const int bn = (N % 256 == 0 && tm * (N / 256) >= sms) ? 256 : 128;
     const long long tiles = tm * (N / bn);
     const unsigned grid = unsigned(tiles < sms ? tiles : sms);
-    if (bn == 256)
-        fwr::umma::gemm_kernel<256, GEMM_BK, OutT>
-            <<<grid, fwr::umma::THREADS, fwr::umma::Cfg<256, GEMM_BK>::SMEM, s>>>(ma, mb256, M, int(N), K, D, ldd,
-                                                                              status, wait_limit);
-    else
-        fwr::umma::gemm_kernel<128, GEMM_BK, OutT>
-            <<<grid, fwr::umma::THREADS, fwr::umma::Cfg<128, GEMM_BK>::SMEM, s>>>(ma, mb128, M, int(N), K, D, ldd,
-                                                                              status, wait_limit);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(fwr::umma::THREADS);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    const int n32 = int(N);
+    if (bn == 256) {
+        cfg.dynamicSmemBytes = fwr::umma::Cfg<256, GEMM_BK>::SMEM;
+        return cudaLaunchKernelEx(&cfg, fwr::umma::gemm_kernel<256, GEMM_BK, OutT>, ma, mb256, M, n32, K, D, ldd,
+                                  status, wait_limit);
+    }
+    cfg.dynamicSmemBytes = fwr::umma::Cfg<128, GEMM_BK>::SMEM;
+    return cudaLaunchKernelEx(&cfg, fwr::umma::gemm_kernel<128, GEMM_BK, OutT>, ma, mb128, M, n32, K, D, ldd, status,
+                              wait_limit);
 }
 
 }  // namespace
@@ -140,6 +151,8 @@ namespace {
 // One block per frame; pairs of columns per thread (ldx even).
 __global__ void k_gather(const float* __restrict__ sl, const int2* __restrict__ src, int nn, int ldx,
                          __nv_bfloat16* __restrict__ X) {
+    // the GEMM after this kernel may start its set-up (it waits for this grid)
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
     const int f = blockIdx.x;
     const float* s = sl + size_t(f) * 2 * nn;
     __nv_bfloat162* x = reinterpret_cast<__nv_bfloat162*>(X + size_t(f) * ldx);
@@ -337,11 +350,13 @@ template <typename OutT>
 cudaError_t run_ws(fwr_linws* w, const float* slopes, int F, OutT* out, cudaStream_t s) {
     k_gather<<<F, 256, 0, s>>>(slopes, reinterpret_cast<const int2*>(w->d_src), w->n * w->n, w->Kpad, w->X);
     cudaError_t e = cudaGetLastError();
+    // the GEMMs are programmatic dependents of their producers (gather, X A)
     if (e == cudaSuccess)
         e = launch_gemm<__nv_bfloat16>(w->mX, w->mAt128, w->mAt256, F, w->rank, w->Kpad, w->C, w->rank, w->d_status,
-                                       s);
+                                       s, fwr::umma::WAIT_LIMIT, true);
     if (e == cudaSuccess)
-        e = launch_gemm<OutT>(w->mC, w->mV128, w->mV256, F, w->cells2, w->rank, out, w->cells2, w->d_status, s);
+        e = launch_gemm<OutT>(w->mC, w->mV128, w->mV256, F, w->cells2, w->rank, out, w->cells2, w->d_status, s,
+                              fwr::umma::WAIT_LIMIT, true);
     return e;
 }
 
@@ -371,7 +386,7 @@ fwr_status fwr_linws_reconstruct(fwr_linws* w, fwr_plan* plan, const float* slop
     cudaError_t e = run_ws<__nv_bfloat16>(w, slopes_dev, n_frames, w->Eh, s);
     if (e == cudaSuccess)
         e = fwr::launch_warm_bf16(plan, slopes_dev, reinterpret_cast<const uint16_t*>(w->Eh), n_frames, iters,
-                                  phase_dev, s);
+                                  phase_dev, s, true);
     if (e == cudaErrorNotSupported)
         return fail(FWR_ERR_UNSUPPORTED, "fwr_linws_reconstruct: the plan does not take the fused path");
     return e == cudaSuccess ? FWR_OK : fwr::cuda_fail(e, "fwr_linws_reconstruct");

@@ -40,9 +40,11 @@ namespace fwr {
 // The FP32 path of plan p through the fused kernel with a BF16 warm start
 // ([F][2][N][N] bit patterns, 8-byte aligned); cudaErrorNotSupported when the
 // plan does not take the fused path (N = 256, the DFT-GEMM transform, grids
-// the fused kernel does not cover).
+// the fused kernel does not cover). pdl: launched as a programmatic
+// dependent of the kernel before it on s, which must be the producer of
+// ext_init_h (its set-up then overlaps that kernel's tail).
 cudaError_t launch_warm_bf16(fwr_plan* p, const float* slopes, const uint16_t* ext_init_h, int n_frames, int iters,
-                             float* phase, cudaStream_t s);
+                             float* phase, cudaStream_t s, bool pdl = false);
 }  // namespace fwr
 
 struct fwr_plan {

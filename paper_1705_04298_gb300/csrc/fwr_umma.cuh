@@ -280,6 +280,11 @@ __global__ void __launch_bounds__(THREADS, 1)
     __syncthreads();
     fence_after();
     const uint32_t tmem = *tmem_slot;
+    // programmatic dependent launch: the next grid may start its own set-up
+    // once every CTA of this one is resident; this grid's inputs are read only
+    // after the grid it depends on (if any) has completed
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
 
     if (warp == 0) {
         if (lane == 0) {
