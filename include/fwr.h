@@ -85,9 +85,11 @@ typedef enum {
                                        operands (x = hi + lo, products hi*hi + hi*lo + lo*hi,
                                        FP32 accumulation). N = 32 or 64: per-frame mma.sync
                                        products in one kernel. N = 128 or 256: batched tcgen05
-                                       GEMMs over chunks of frames (two per 2-D transform) with
-                                       element-wise kernels between them; setting the option
-                                       allocates the plan's workspace (about 170 MB) and the
+                                       GEMMs over chunks of frames (two per 2-D transform; the
+                                       first writes the second's split operand from its
+                                       epilogue) with element-wise kernels between transforms;
+                                       setting the option allocates the plan's workspace
+                                       (about 270 MB) and the
                                        reconstruct calls allocate nothing; no ext_out (returns
                                        FWR_ERR_UNSUPPORTED). Other N: FWR_ERR_UNSUPPORTED.
                                        About 2e-5 relative phase error (stated by the tests) */
@@ -98,8 +100,8 @@ typedef enum {
                                        (about 2e-5: the tensor core's FP32 accumulation over K,
                                        not the operand split, sets it). Other N:
                                        FWR_ERR_UNSUPPORTED.
-                                       Setting it allocates its own workspace (about 280 MB at
-                                       256^2), replacing a DFT_BF16X3 one (the plan falls back to
+                                       Setting it allocates its own workspace (about 480 MB),
+                                       replacing a DFT_BF16X3 one (the plan falls back to
                                        the FFT transform if that allocation fails) */
 /* Values of FWR_OPT_PERIODIC: where Eq. PC is applied. */
 #define FWR_PERIODIC_BEFORE_EACH_FFT 0 /* before every forward FFT, the final one included (default) */

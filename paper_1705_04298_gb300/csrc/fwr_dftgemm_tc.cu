@@ -23,11 +23,14 @@
 //   right product  B rows (f, r) = row r of Z_f        -> D [2N][(f, r)] = (Z_f F)^T
 //   left product   B rows (f, i) = column i of Z_f F   -> D [2N][(f, k)] = F Z_f F
 // so D's rows are output rows (real parts, then imaginary parts) and its
-// columns run over frames and the other index. Between the GEMMs, element-wise
-// kernels rebuild B from D: the plain re-split, the spectral step (LSQ
-// projection or final filter, with the y part of Eq. PC as a spectral
-// correction) and, in direct space, reinsertion of the measured slopes and the
-// x part of Eq. PC.
+// columns run over frames and the other index. The right product's epilogue
+// writes its result straight into the left product's operand, split into BF16
+// terms (B row (f, i) = [Re D[i][(f, .)], Im D[N + i][(f, .)]]; no FP32 D in
+// between). After the left products, element-wise kernels rebuild B from D:
+// the spectral step (LSQ projection or final filter, with the y part of Eq.
+// PC as a spectral correction; it needs the partner bins (-ky, -kx), which
+// lie in other tiles) and, in direct space, reinsertion of the measured
+// slopes and the x part of Eq. PC (row sums over whole rows).
 
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -52,7 +55,8 @@ __host__ __device__ inline int gemm_k(int N, int terms) { return 2 * N * terms; 
 struct Ws {
     bf16* Af;  // [2N][K] forward operand
     bf16* Ai;  // [2N][K] inverse operand
-    bf16* B;   // [chunk N][K]
+    bf16* B;   // [chunk N][K]: operand of each transform's right product
+    bf16* B2;  // [chunk N][K]: operand of its left product (the right product's split epilogue)
     float* D;  // [2N][chunk N]
 };
 
@@ -62,10 +66,12 @@ Ws carve(int N, int terms, void* ws) {
     const size_t K = size_t(gemm_k(N, terms));
     const size_t a = size_t(2 * N) * K * sizeof(bf16);
     const size_t cols = size_t(chunk_frames(N)) * N;
+    const size_t b = cols * K * sizeof(bf16);
     w.Af = reinterpret_cast<bf16*>(p);
     w.Ai = reinterpret_cast<bf16*>(p + a);
     w.B = reinterpret_cast<bf16*>(p + 2 * a);
-    w.D = reinterpret_cast<float*>(p + 2 * a + cols * K * sizeof(bf16));
+    w.B2 = reinterpret_cast<bf16*>(p + 2 * a + b);
+    w.D = reinterpret_cast<float*>(p + 2 * a + 2 * b);
     return w;
 }
 
@@ -196,21 +202,6 @@ __global__ void k_dg_rows(const float* D, long long ldd, bool embed, const float
     }
 }
 
-// D (rows: output index, real then imaginary; columns (f, x)) -> B rows
-// (f, i) = [Re D[i][(f, .)], Im D[N + i][(f, .)]] split: the next product's
-// operand. One block of N / 2 threads per B row.
-__global__ void k_dg_resplit(const float* D, long long ldd, int N, bf16* B, int terms) {
-    const int row = blockIdx.x;
-    const int fl = row / N, i = row % N;
-    bf16* b = B + (size_t)row * gemm_k(N, terms);
-#pragma unroll
-    for (int u = 0; u < 2; ++u) {
-        const int x = threadIdx.x + u * (N / 2);
-        put_split(b, N, x, D[(size_t)i * ldd + (size_t)fl * N + x], terms);
-        put_split(b, N, N + x, D[(size_t)(N + i) * ldd + (size_t)fl * N + x], terms);
-    }
-}
-
 // Spectral step on Y_f[ky][kx] = D[ky][(f, kx)] + i D[N + ky][(f, kx)], the
 // packed spectrum of sx + i sy; writes B rows (f, ky) of the inverse's right
 // product. Non-final: LSQ projection (Algorithm 1 steps 2-3); final: the
@@ -269,7 +260,7 @@ __global__ void k_dg_phase(const float* D, long long ldd, int N, int f0, int nf,
 size_t dftgemm_ws_bytes(int N, int terms) {
     if ((N != 128 && N != 256) || (terms != 3 && terms != 6)) return 0;
     const size_t cols = size_t(chunk_frames(N)) * N, K = size_t(gemm_k(N, terms));
-    return 2 * size_t(2 * N) * K * sizeof(bf16) + cols * K * sizeof(bf16) + size_t(2 * N) * cols * sizeof(float);
+    return 2 * size_t(2 * N) * K * sizeof(bf16) + 2 * cols * K * sizeof(bf16) + size_t(2 * N) * cols * sizeof(float);
 }
 
 int dftgemm_chunk(int N) { return chunk_frames(N); }
@@ -298,24 +289,17 @@ cudaError_t launch_dftgemm_f32(int N, int terms, const Params<float>& p, void* w
             k_dg_rows<<<nf * N, N / 2, 0, s>>>(w.D, ldd, it == 0, p.slopes, p.ext_init, p.mask, p.n, p.off, N, f0,
                                                fill, w.B, p.status, terms);
             cudaError_t e = cudaGetLastError();
-            // forward transform: right product, re-split, left product
-            if (e == cudaSuccess) e = tc_gemm(w.Af, 2 * N, K, w.B, cols, w.D, false, ldd, st, s);
-            if (e == cudaSuccess) {
-                k_dg_resplit<<<nf * N, N / 2, 0, s>>>(w.D, ldd, N, w.B, terms);
-                e = cudaGetLastError();
-            }
-            if (e == cudaSuccess) e = tc_gemm(w.Af, 2 * N, K, w.B, cols, w.D, false, ldd, st, s);
+            // forward transform: right product (its epilogue splits the result
+            // into the left product's operand B2), left product
+            if (e == cudaSuccess) e = tc_gemm_split(w.Af, 2 * N, K, w.B, cols, w.B2, N, K, terms, st, s);
+            if (e == cudaSuccess) e = tc_gemm(w.Af, 2 * N, K, w.B2, cols, w.D, false, ldd, st, s);
             if (e == cudaSuccess) {
                 k_dg_spectral<<<nf * N, N / 2, 0, s>>>(w.D, ldd, N, p.tab, final, fill, w.B, terms);
                 e = cudaGetLastError();
             }
             // inverse transform
-            if (e == cudaSuccess) e = tc_gemm(w.Ai, 2 * N, K, w.B, cols, w.D, false, ldd, st, s);
-            if (e == cudaSuccess) {
-                k_dg_resplit<<<nf * N, N / 2, 0, s>>>(w.D, ldd, N, w.B, terms);
-                e = cudaGetLastError();
-            }
-            if (e == cudaSuccess) e = tc_gemm(w.Ai, 2 * N, K, w.B, cols, w.D, false, ldd, st, s);
+            if (e == cudaSuccess) e = tc_gemm_split(w.Ai, 2 * N, K, w.B, cols, w.B2, N, K, terms, st, s);
+            if (e == cudaSuccess) e = tc_gemm(w.Ai, 2 * N, K, w.B2, cols, w.D, false, ldd, st, s);
             if (e != cudaSuccess) return e;
         }
         if (p.phase) {

@@ -145,6 +145,13 @@ cudaError_t launch_fft2_f32(int N, const float2* in, float2* out, int F, int inv
 // *status.
 cudaError_t tc_gemm(const void* A, int M, int K, const void* B, long long N, void* D, bool bf16_out, long long ldd,
                     int* status, cudaStream_t s);
+// The same product (M = 2n) with its output split into BF16 terms and written
+// as the next product's B operand: output (i, (f, x)), column (f, x) = f n + x,
+// goes to row f n + (i mod n) of Bout [.][kout = 2 n terms], column x (+ n for
+// i >= n), in each term region (3 terms: hi, lo, hi; 6: h, m, h, l, m, h).
+// Bout must not be the operand B of the same call.
+cudaError_t tc_gemm_split(const void* A, int M, int K, const void* B, long long N, void* Bout, int n, int kout,
+                          int terms, int* status, cudaStream_t s);
 
 // Batched split-BF16 DFT-as-GEMM path for N = 128 and 256 (fwr_dftgemm_tc.cu):
 // every 2-D transform of Algorithm 1 and of the final reconstruction as two

@@ -97,7 +97,8 @@ int device_sms(int device) {
 template <typename OutT>
 cudaError_t launch_gemm(const CUtensorMap& ma, const CUtensorMap& mb128, const CUtensorMap& mb256, int M,
                         long long N, int K, OutT* D, long long ldd, int* status, cudaStream_t s,
-                        long long wait_limit = fwr::umma::WAIT_LIMIT, bool pdl = false) {
+                        long long wait_limit = fwr::umma::WAIT_LIMIT, bool pdl = false,
+                        fwr::umma::SplitDst sd = fwr::umma::SplitDst()) {
     int dev = 0;
     cudaGetDevice(&dev);
     const int sms = device_sms(dev);
@@ -119,11 +120,11 @@ cudaError_t launch_gemm(const CUtensorMap& ma, const CUtensorMap& mb128, const C
     if (bn == 256) {
         cfg.dynamicSmemBytes = fwr::umma::Cfg<256, GEMM_BK>::SMEM;
         return cudaLaunchKernelEx(&cfg, fwr::umma::gemm_kernel<256, GEMM_BK, OutT>, ma, mb256, M, n32, K, D, ldd,
-                                  status, wait_limit);
+                                  status, wait_limit, sd);
     }
     cfg.dynamicSmemBytes = fwr::umma::Cfg<128, GEMM_BK>::SMEM;
     return cudaLaunchKernelEx(&cfg, fwr::umma::gemm_kernel<128, GEMM_BK, OutT>, ma, mb128, M, n32, K, D, ldd, status,
-                              wait_limit);
+                              wait_limit, sd);
 }
 
 }  // namespace
@@ -141,6 +142,26 @@ cudaError_t fwr::tc_gemm(const void* A, int M, int K, const void* B, long long N
     return bf16_out ? launch_gemm<__nv_bfloat16>(ma, mb128, mb256, M, N, K, static_cast<__nv_bfloat16*>(D), ldd,
                                                  status, s)
                     : launch_gemm<float>(ma, mb128, mb256, M, N, K, static_cast<float*>(D), ldd, status, s);
+}
+
+// The same product with the split-BF16 epilogue (fwr_umma.cuh SplitDst):
+// output (i, (f, x)) -> BF16 terms in row f n + (i mod n) of Bout [.][kout].
+cudaError_t fwr::tc_gemm_split(const void* A, int M, int K, const void* B, long long N, void* Bout, int n, int kout,
+                               int terms, int* status, cudaStream_t s) {
+    if (M < 1 || M != 2 * n || K < 8 || K % 8 != 0 || N < 128 || N % 128 != 0 || n % 64 != 0 ||
+        kout != 2 * n * terms || (terms != 3 && terms != 6) || !Bout)
+        return cudaErrorInvalidValue;
+    CUtensorMap ma, mb128, mb256;
+    if (!make_map(&ma, A, uint64_t(K), uint64_t(M), uint64_t(K), BM) ||
+        !make_map(&mb128, B, uint64_t(K), uint64_t(N), uint64_t(K), 128) ||
+        !make_map(&mb256, B, uint64_t(K), uint64_t(N), uint64_t(K), 256))
+        return cudaErrorInvalidValue;
+    fwr::umma::SplitDst sd;
+    sd.B = static_cast<__nv_bfloat16*>(Bout);
+    sd.n = n;
+    sd.k = kout;
+    sd.terms = terms;
+    return launch_gemm<float>(ma, mb128, mb256, M, N, K, nullptr, 0, status, s, fwr::umma::WAIT_LIMIT, false, sd);
 }
 
 namespace {

@@ -14,7 +14,9 @@
 //                    into one of two TMEM accumulators (2 BN columns in all),
 //                    tcgen05.commit to the stage's "empty" mbarrier and, after
 //                    a tile's last k-block, to the accumulator's "full" barrier
-//   warps 2-5        epilogue: tcgen05.ld of their 32 accumulator lanes
+//   warps 2-5        epilogue (or, with a SplitDst, BF16 terms of each value
+//                    written straight into the next product's B operand):
+//                    tcgen05.ld of their 32 accumulator lanes
 //                    (rows; warp w reads lanes 32 (w mod 4) ..), conversion,
 //                    a pass through a swizzled shared tile so that each store
 //                    instruction writes four whole 128-byte rows, then an
@@ -218,6 +220,82 @@ __device__ __forceinline__ void epilogue_segment(uint32_t tw, uint4* tile, OutT*
     __syncwarp();
 }
 
+// Destination of the split epilogue: instead of D[M][ldd] (FP32), each output
+// (row i, column (f, x) with f = column / n, x = column mod n) goes to the
+// next product's B operand as BF16 terms: row f n + (i mod n) of B [.][k],
+// column x + n (i >= n), in the term regions of split_b: 3 terms: [hi | lo |
+// hi] at 0, 2n, 4n; 6 terms: [h | m | h | l | m | h] at 0, 2n, .., 10n.
+struct SplitDst {
+    __nv_bfloat16* B = nullptr;
+    int n = 0, k = 0, terms = 0;
+};
+
+// term t (0: h, 1: m, 2: l) of x: h = bf16(x), m = bf16(x - h), l = bf16(x - h - m)
+__device__ __forceinline__ uint32_t split_term_bits(float x, int t) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(x);
+    if (t == 0) return __bfloat16_as_ushort(h);
+    const float r = x - __bfloat162float(h);
+    const __nv_bfloat16 m = __float2bfloat16_rn(r);
+    if (t == 1) return __bfloat16_as_ushort(m);
+    return __bfloat16_as_ushort(__float2bfloat16_rn(r - __bfloat162float(m)));
+}
+
+// One 64-column segment of a warp's 32 accumulator rows to the split
+// destination. Per term: the lanes' rows (64 BF16 values, 128 bytes each)
+// pass through the warp's swizzled shared tile (16-byte chunk c of row r at
+// c ^ (r mod 8)), then each store instruction writes four whole 128-byte rows
+// to every term region that holds the term. col0: the segment's first output
+// column (a multiple of 64, within one frame since n is a multiple of 64).
+__device__ __forceinline__ void epilogue_split_segment(uint32_t tw, uint4* tile, const SplitDst& sd, int m0w,
+                                                       int col0, int lane) {
+    uint32_t v[64];
+    {
+        uint32_t (&v0)[32] = *reinterpret_cast<uint32_t(*)[32]>(v);
+        uint32_t (&v1)[32] = *reinterpret_cast<uint32_t(*)[32]>(v + 32);
+        tmem_ld32(tw, v0);
+        tmem_ld32(tw + 32u, v1);
+    }
+    const int f = col0 / sd.n, x = col0 % sd.n;
+    const size_t region = size_t(2 * sd.n);
+    const int c = lane & 7;
+    const int nterms = sd.terms == 6 ? 3 : 2;
+#pragma unroll 1
+    for (int t = 0; t < nterms; ++t) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            uint32_t w[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                w[j] = split_term_bits(__uint_as_float(v[8 * q + 2 * j]), t) |
+                       (split_term_bits(__uint_as_float(v[8 * q + 2 * j + 1]), t) << 16);
+            tile[lane * 8 + (q ^ (lane & 7))] = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+        __syncwarp();
+        // regions of term t: 3 terms [h | m | h]; 6 terms [h | m | h | l | m | h]
+        int reg[3], nreg;
+        if (sd.terms == 3) {
+            nreg = t == 0 ? 2 : 1;
+            reg[0] = t == 0 ? 0 : 1;
+            reg[1] = 2;
+        } else {
+            nreg = t == 0 ? 3 : (t == 1 ? 2 : 1);
+            reg[0] = t == 0 ? 0 : (t == 1 ? 1 : 3);
+            reg[1] = t == 0 ? 2 : 4;
+            reg[2] = 5;
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int r = 4 * i + (lane >> 3);
+            const uint4 val = tile[r * 8 + (c ^ (r & 7))];
+            const int row = m0w + r;
+            __nv_bfloat16* const b =
+                sd.B + (size_t(f) * sd.n + (row % sd.n)) * sd.k + (row >= sd.n ? sd.n : 0) + x + 8 * c;
+            for (int g = 0; g < nreg; ++g) *reinterpret_cast<uint4*>(b + reg[g] * region) = val;
+        }
+        __syncwarp();
+    }
+}
+
 // bounded wait without an abort check (draining work already issued)
 __device__ __forceinline__ void mbar_drain(uint32_t bar, uint32_t parity, volatile int* abort) {
     const long long t0 = clock64();
@@ -237,7 +315,7 @@ __device__ __forceinline__ void mbar_drain(uint32_t bar, uint32_t parity, volati
 template <int BN, int BK, typename OutT>
 __global__ void __launch_bounds__(THREADS, 1)
     gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int M, int N,
-                int K, OutT* __restrict__ D, long long ldd, int* status, long long wait_limit) {
+                int K, OutT* __restrict__ D, long long ldd, int* status, long long wait_limit, SplitDst sd) {
     typedef Cfg<BN, BK> C;
     constexpr int S = C::STAGES;
     extern __shared__ uint8_t smem_raw[];
@@ -353,9 +431,15 @@ __global__ void __launch_bounds__(THREADS, 1)
             const int m0 = (t % tiles_m) * BM, n0 = (t / tiles_m) * BN;
             const uint32_t tw = tmem + uint32_t(b * BN) + (uint32_t(q * 32) << 16);
             uint4* const tile = epi + (warp - 2) * 256;
+            if (sd.B) {
 #pragma unroll 1
-            for (int c = 0; c < BN; c += Epi<OutT>::COLS)
-                epilogue_segment<OutT>(tw + uint32_t(c), tile, D + n0 + c, ldd, m0 + q * 32, M, lane);
+                for (int c = 0; c < BN; c += 64)
+                    epilogue_split_segment(tw + uint32_t(c), tile, sd, m0 + q * 32, n0 + c, lane);
+            } else {
+#pragma unroll 1
+                for (int c = 0; c < BN; c += Epi<OutT>::COLS)
+                    epilogue_segment<OutT>(tw + uint32_t(c), tile, D + n0 + c, ldd, m0 + q * 32, M, lane);
+            }
             fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(acce0 + 8 * b);
