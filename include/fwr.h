@@ -83,8 +83,8 @@ typedef enum {
 #define FWR_TRANSFORM_FFT 0         /* shared-memory FFT (default) */
 #define FWR_TRANSFORM_DFT_BF16X3 1  /* dense DFT products on the tensor cores with split-BF16
                                        operands (x = hi + lo, products hi*hi + hi*lo + lo*hi,
-                                       FP32 accumulation). N = 32 or 64: per-frame mma.sync
-                                       products in one kernel. N = 128 or 256: batched tcgen05
+                                       FP32 accumulation). N = 32: per-frame mma.sync
+                                       products in one kernel. N = 64, 128 or 256: batched tcgen05
                                        GEMMs over chunks of frames (two per 2-D transform; the
                                        first writes the second's split operand from its
                                        epilogue) with element-wise kernels between transforms;
@@ -93,7 +93,7 @@ typedef enum {
                                        reconstruct calls allocate nothing; no ext_out (returns
                                        FWR_ERR_UNSUPPORTED). Other N: FWR_ERR_UNSUPPORTED.
                                        About 2e-5 relative phase error (stated by the tests) */
-#define FWR_TRANSFORM_DFT_BF16X6 2  /* the batched tcgen05 DFT-as-GEMM path of N = 128 and 256
+#define FWR_TRANSFORM_DFT_BF16X6 2  /* the batched tcgen05 DFT-as-GEMM path of N = 64, 128 and 256
                                        with a three-way BF16 split (x = hi + mid + lo) and six
                                        products (hh + hm + mh + hl + mm + lh) over K = 12N: twice
                                        the GEMM work of DFT_BF16X3 for the same measured error

@@ -418,9 +418,9 @@ fwr_status fwr_plan_set_option(fwr_plan* p, int key, double value) {
             return FWR_ERR_ARG;
         if (v == FWR_TRANSFORM_DFT_BF16X3 && p->N != 32 && p->N != 64 && p->N != 128 && p->N != 256)
             return FWR_ERR_UNSUPPORTED;  // (non-power-of-two grids included)
-        if (v == FWR_TRANSFORM_DFT_BF16X6 && p->N != 128 && p->N != 256) return FWR_ERR_UNSUPPORTED;
+        if (v == FWR_TRANSFORM_DFT_BF16X6 && p->N != 64 && p->N != 128 && p->N != 256) return FWR_ERR_UNSUPPORTED;
         const int terms = v == FWR_TRANSFORM_DFT_BF16X6 ? 6 : 3;
-        if (v != FWR_TRANSFORM_FFT && p->N >= 128 && (!p->d_dftws || p->dftws_terms != terms)) {
+        if (v != FWR_TRANSFORM_FFT && p->N >= 64 && (!p->d_dftws || p->dftws_terms != terms)) {
             // batched tensor-core path: its workspace is made here, not in the
             // reconstruct calls (one for the other product count is freed first,
             // after a device synchronisation)
@@ -560,7 +560,7 @@ fwr_status fwr_reconstruct_ex(fwr_plan* p, const float* slopes, const float* ext
     if (!pow2(p->N)) {
         e = fwr::launch_anygrid_f32(p->N, k, static_cast<cudaStream_t>(stream));
     } else if (p->transform != FWR_TRANSFORM_FFT) {
-        if (p->N >= 128) {
+        if (p->N >= 64) {
             if (ext_out || !phase) return FWR_ERR_UNSUPPORTED;
             e = fwr::launch_dftgemm_f32(p->N, p->dftws_terms, k, p->d_dftws, static_cast<cudaStream_t>(stream));
         } else {

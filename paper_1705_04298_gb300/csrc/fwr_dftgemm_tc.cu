@@ -1,4 +1,4 @@
-// Split-BF16 DFT-as-GEMM path for 128^2 and 256^2 grids on the tcgen05 tensor
+// Split-BF16 DFT-as-GEMM path for 64^2, 128^2 and 256^2 grids on the tcgen05 tensor
 // cores: Algorithm 1 (Sec. 3.3) and the final reconstruction (Eqs. 2-3) with
 // every 2-D DFT computed as dense products, Z <- F Z F with F[j][k] =
 // e^{-2 i pi j k / N} (the conjugate for the inverse; no scaling: 1/N^2 is in
@@ -258,7 +258,7 @@ __global__ void k_dg_phase(const float* D, long long ldd, int N, int f0, int nf,
 }  // namespace
 
 size_t dftgemm_ws_bytes(int N, int terms) {
-    if ((N != 128 && N != 256) || (terms != 3 && terms != 6)) return 0;
+    if ((N != 64 && N != 128 && N != 256) || (terms != 3 && terms != 6)) return 0;
     const size_t cols = size_t(chunk_frames(N)) * N, K = size_t(gemm_k(N, terms));
     return 2 * size_t(2 * N) * K * sizeof(bf16) + 2 * cols * K * sizeof(bf16) + size_t(2 * N) * cols * sizeof(float);
 }
@@ -273,7 +273,7 @@ cudaError_t dftgemm_setup(int N, int terms, const float2* tw, void* ws) {
 }
 
 cudaError_t launch_dftgemm_f32(int N, int terms, const Params<float>& p, void* ws, cudaStream_t s) {
-    if ((N != 128 && N != 256) || (terms != 3 && terms != 6) || !ws) return cudaErrorInvalidValue;
+    if ((N != 64 && N != 128 && N != 256) || (terms != 3 && terms != 6) || !ws) return cudaErrorInvalidValue;
     const Ws w = carve(N, terms, ws);
     const int K = gemm_k(N, terms);
     const int chunk = chunk_frames(N);
@@ -281,8 +281,11 @@ cudaError_t launch_dftgemm_f32(int N, int terms, const Params<float>& p, void* w
     int* st = reinterpret_cast<int*>(p.status);
     for (int f0 = 0; f0 < p.F; f0 += chunk) {
         const int nf = p.F - f0 < chunk ? p.F - f0 : chunk;
-        // GEMM columns: whole frames of N >= 128 columns, a multiple of 128
-        const long long cols = (long long)nf * N;
+        // GEMM columns: whole frames, rounded up to a multiple of 128 (at 64^2
+        // an odd frame count adds one frame's columns, whose B rows hold stale
+        // values: each output column depends on its own B row only, and no
+        // kernel reads those columns back)
+        const long long cols = ((long long)nf * N + 127) / 128 * 128;
         for (int it = 0; it <= p.iters; ++it) {
             const bool final = it == p.iters;
             const bool fill = p.periodic == PERIODIC_BEFORE_EACH_FFT || (p.periodic == PERIODIC_FINAL_ONLY && final);

@@ -153,7 +153,7 @@ cudaError_t tc_gemm(const void* A, int M, int K, const void* B, long long N, voi
 cudaError_t tc_gemm_split(const void* A, int M, int K, const void* B, long long N, void* Bout, int n, int kout,
                           int terms, int* status, cudaStream_t s);
 
-// Batched split-BF16 DFT-as-GEMM path for N = 128 and 256 (fwr_dftgemm_tc.cu):
+// Batched split-BF16 DFT-as-GEMM path for N = 64, 128 and 256 (fwr_dftgemm_tc.cu):
 // every 2-D transform of Algorithm 1 and of the final reconstruction as two
 // tcgen05 GEMMs over a chunk of frames. Workspace: dftgemm_ws_bytes(N) bytes.
 // terms: 3 or 6 split products (FWR_TRANSFORM_DFT_BF16X3 / X6).

@@ -71,7 +71,7 @@ struct fwr_plan {
     // 256^2 grids: device address of the library's static scratch array on the
     // plan's device (looked up at plan creation; nullptr if that failed)
     float2* d_static_scratch = nullptr;
-    // DFT-as-GEMM transform on 128^2 / 256^2 grids: operands and chunk buffers
+    // DFT-as-GEMM transform on 64^2 / 128^2 / 256^2 grids: operands and chunk buffers
     void* d_dftws = nullptr;
     int dftws_terms = 0;  // split products the workspace was built for (3 or 6)
     int scratch_ctas = 0;

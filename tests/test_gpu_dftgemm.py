@@ -1,6 +1,6 @@
 """Precision variant: 2-D transforms as dense DFT products on the tensor cores
 with split-BF16 operands (FWR_TRANSFORM_DFT_BF16X3): per-frame mma.sync
-products for 32^2 and 64^2 grids, batched tcgen05 GEMMs for 128^2 and 256^2.
+products for 32^2 grids, batched tcgen05 GEMMs for 64^2, 128^2 and 256^2.
 The transform is checked against numpy's FFT, and whole reconstructions with
 it against the FP64 oracle; the measured errors are printed (pytest -s) and
 bounded here. A BF16 pair keeps 16 significant bits, so about 1e-5 per
@@ -114,6 +114,29 @@ def test_batched_tensor_core_dft_chunks_and_limits(fwr):
     assert e.value.code == 2
 
 
+def test_batched_dft_64_grid_odd_frames_and_chunks(fwr):
+    """64^2 through the batched tcgen05 GEMMs: an odd frame count (the GEMM
+    columns are rounded up to 128, one frame's worth of padding) and more
+    frames than one chunk (2048 at 64^2). Identical inputs give identical
+    phases in either chunk, and the frames agree with the oracle."""
+    n, pad, k = 30, 2.0, 3
+    sl, _, mask = synth.batch(n, 3, 950, 0.05)
+    plan = fwr.Plan(mask, pad, fwr.LSQ)
+    assert plan.N == 64
+    plan.set_transform(fwr.TRANSFORM_DFT_BF16X3)
+    s = torch.tensor(sl, dtype=torch.float32, device="cuda").repeat(683, 1, 1, 1)  # 2049 frames
+    ph = plan.reconstruct(s, k)
+    assert plan.status() == "FWR_OK"
+    assert torch.isfinite(ph).all()
+    assert torch.equal(ph[0], ph[2046]) and torch.equal(ph[1], ph[2047]) and torch.equal(ph[2], ph[2048])
+    one = plan.reconstruct(s[:1], k)
+    assert torch.equal(one[0], ph[0])
+    ph = ph.cpu().numpy()
+    for f in range(3):
+        ref, _ = oracle.reconstruct(sl[f], mask, pad, k, oracle.FILTER_LSQ)
+        assert within(ph[f], ref, DFT_RMS, DFT_MAX, where="64^2 f=%d" % f)
+
+
 def test_transform_option_limits(fwr):
     plan = fwr.Plan(synth.pupil_mask(12), 1.25, fwr.LSQ)  # 16^2: no tensor-core DFT
     assert plan.N == 16
@@ -125,7 +148,7 @@ def test_transform_option_limits(fwr):
 
 
 @pytest.mark.parametrize("n,pad,k,filt,periodic", [(40, 3.2, 10, "wiener", 0), (80, 3.2, 5, "lsq", 0),
-                                                    (128, 2.0, 2, "lsq", 1)])
+                                                    (128, 2.0, 2, "lsq", 1), (30, 2.0, 4, "wiener", 0)])
 def test_six_product_split(fwr, n, pad, k, filt, periodic):
     """FWR_TRANSFORM_DFT_BF16X6: the three-way BF16 split with six products
     per real product represents every operand to about 24 bits, yet the
