@@ -137,24 +137,36 @@ def _check(code, where):
         raise FwrError(code, where)
 
 
+# Argument marshalling is on every call's path (a call on an idle GPU waits
+# for it), so it is kept lean: pointers and streams go to ctypes as plain
+# integers (the argtypes convert them) and the checks are attribute compares.
+
 def _ptr(t):
-    return None if t is None else ctypes.c_void_p(t.data_ptr())
+    return None if t is None else t.data_ptr()
 
 
-def _stream(stream):
+def _stream(stream, device=None):
+    """The raw handle of `stream`, or of the current stream of `device` (the
+    current device when None)."""
     import torch
-    if stream is None:
-        stream = torch.cuda.current_stream()
-    return ctypes.c_void_p(stream.cuda_stream)
+    if stream is not None:
+        return stream.cuda_stream
+    raw = getattr(torch._C, "_cuda_getCurrentRawStream", None)
+    if raw is not None:  # the current stream without building a Stream object
+        return raw(torch.cuda.current_device() if device is None else device)
+    return torch.cuda.current_stream(device).cuda_stream
 
 
 def _need(t, dtype, shape, name):
-    import torch
     if t is None:
         return
-    if not isinstance(t, torch.Tensor) or t.dtype != dtype or tuple(t.shape) != tuple(shape):
-        raise ValueError("%s must be a %s tensor of shape %s" % (name, dtype, tuple(shape)))
-    if not t.is_cuda or not t.is_contiguous():
+    try:
+        ok = t.dtype == dtype and t.shape == shape and t.is_cuda and t.is_contiguous()
+    except (AttributeError, TypeError):
+        ok = False
+    if not ok:
+        if getattr(t, "dtype", None) != dtype or tuple(getattr(t, "shape", ())) != tuple(shape):
+            raise ValueError("%s must be a %s tensor of shape %s" % (name, dtype, tuple(shape)))
         raise ValueError("%s must be a contiguous CUDA tensor" % name)
 
 
@@ -271,7 +283,7 @@ class Plan:
         _need(ext_init, torch.float32, (F, 2, N, N), "ext_init")
         _need(ext_out, torch.float32, (F, 2, N, N), "ext_out")
         _check(self._lib.fwr_reconstruct_ex(self._h, _ptr(slopes), _ptr(ext_init), F, int(iters),
-                                            _ptr(phase), _ptr(ext_out), _stream(stream)),
+                                            _ptr(phase), _ptr(ext_out), _stream(stream, slopes.device.index)),
                "fwr_reconstruct_ex")
         return phase
 
