@@ -68,9 +68,9 @@ bool make_map(CUtensorMap* map, const void* ptr, uint64_t cols, uint64_t rows, u
                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int BN, typename OutT>
+template <int BN, typename OutT, bool SPLIT = false>
 cudaError_t set_smem() {
-    return cudaFuncSetAttribute(fwr::umma::gemm_kernel<BN, GEMM_BK, OutT>,
+    return cudaFuncSetAttribute(fwr::umma::gemm_kernel<BN, GEMM_BK, OutT, SPLIT>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, int(fwr::umma::Cfg<BN, GEMM_BK>::SMEM));
 }
 
@@ -84,6 +84,7 @@ int device_sms(int device) {
     int sms = 0;
     if (set_smem<128, float>() != cudaSuccess || set_smem<256, float>() != cudaSuccess ||
         set_smem<128, __nv_bfloat16>() != cudaSuccess || set_smem<256, __nv_bfloat16>() != cudaSuccess ||
+        set_smem<128, float, true>() != cudaSuccess || set_smem<256, float, true>() != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || sms < 1)
         return 0;
     done.push_back({device, sms});
@@ -117,14 +118,19 @@ cudaError_t launch_gemm(const CUtensorMap& ma, const CUtensorMap& mb128, const C
     cfg.attrs = attr;
     cfg.numAttrs = pdl ? 1 : 0;
     const int n32 = int(N);
+    const bool split = sd.B != nullptr;
     if (bn == 256) {
         cfg.dynamicSmemBytes = fwr::umma::Cfg<256, GEMM_BK>::SMEM;
-        return cudaLaunchKernelEx(&cfg, fwr::umma::gemm_kernel<256, GEMM_BK, OutT>, ma, mb256, M, n32, K, D, ldd,
-                                  status, wait_limit, sd);
+        return split ? cudaLaunchKernelEx(&cfg, fwr::umma::gemm_kernel<256, GEMM_BK, OutT, true>, ma, mb256, M, n32,
+                                          K, D, ldd, status, wait_limit, sd)
+                     : cudaLaunchKernelEx(&cfg, fwr::umma::gemm_kernel<256, GEMM_BK, OutT, false>, ma, mb256, M, n32,
+                                          K, D, ldd, status, wait_limit, sd);
     }
     cfg.dynamicSmemBytes = fwr::umma::Cfg<128, GEMM_BK>::SMEM;
-    return cudaLaunchKernelEx(&cfg, fwr::umma::gemm_kernel<128, GEMM_BK, OutT>, ma, mb128, M, n32, K, D, ldd, status,
-                              wait_limit, sd);
+    return split ? cudaLaunchKernelEx(&cfg, fwr::umma::gemm_kernel<128, GEMM_BK, OutT, true>, ma, mb128, M, n32, K,
+                                      D, ldd, status, wait_limit, sd)
+                 : cudaLaunchKernelEx(&cfg, fwr::umma::gemm_kernel<128, GEMM_BK, OutT, false>, ma, mb128, M, n32, K,
+                                      D, ldd, status, wait_limit, sd);
 }
 
 }  // namespace

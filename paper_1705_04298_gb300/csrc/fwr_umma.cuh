@@ -312,7 +312,9 @@ __device__ __forceinline__ void mbar_drain(uint32_t bar, uint32_t parity, volati
 // wait_limit bounds the MMA issuer's and the epilogue's waits (WAIT_LIMIT in
 // normal use; a test passes a few cycles to make them run out); the
 // producer's waits and every drain of work in flight keep WAIT_LIMIT.
-template <int BN, int BK, typename OutT>
+// SPLIT: the epilogue writes split BF16 terms to sd instead of D (a separate
+// instantiation, so the plain products keep their register budget).
+template <int BN, int BK, typename OutT, bool SPLIT = false>
 __global__ void __launch_bounds__(THREADS, 1)
     gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int M, int N,
                 int K, OutT* __restrict__ D, long long ldd, int* status, long long wait_limit, SplitDst sd) {
@@ -431,7 +433,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             const int m0 = (t % tiles_m) * BM, n0 = (t / tiles_m) * BN;
             const uint32_t tw = tmem + uint32_t(b * BN) + (uint32_t(q * 32) << 16);
             uint4* const tile = epi + (warp - 2) * 256;
-            if (sd.B) {
+            if constexpr (SPLIT) {
 #pragma unroll 1
                 for (int c = 0; c < BN; c += 64)
                     epilogue_split_segment(tw + uint32_t(c), tile, sd, m0 + q * 32, n0 + c, lane);
