@@ -73,6 +73,10 @@ def test_null_plan_calls(lib):
     assert lib.fwr_plan_set_option(None, 1, 0.0) == 1
     assert lib.fwr_fft2(48, None, None, 1, 0, None) == 1
     assert lib.fwr_fft2(32, None, None, 0, 0, None) == 0
+    assert lib.fwr_plan_shape(None) == -1 and lib.fwr_plan_ctas(None) == -1 and lib.fwr_plan_l2_persist(None) == -1
+    assert lib.fwr_plan_set_option(None, fwr.OPT_L2_PERSIST, 1.0) == 1
+    assert lib.fwr_l2_persist_reset(-1) == 1  # no such device
+    assert lib.fwr_plan_autotune(None, None, 1, 1, None, None, None) == 1
     lib.fwr_plan_destroy(None)
 
 
