@@ -94,6 +94,9 @@ TRAFFIC = {
     # unchanged kernel, internal header comments edited (ncu --metrics dram__bytes_read.sum,
     # dram__bytes_write.sum, bench.py --workload fused128): 13.637 MB + 6.909 MB
     "c42445c2dd37e6f3": 20546560,
+    # the launcher caches its occupancy queries (kernel unchanged; ncu --metrics
+    # dram__bytes_read.sum,dram__bytes_write.sum, bench.py --workload fused128): 13.636 MB + 6.874 MB
+    "87a73a622d7087ed": 20509952,
 }
 
 

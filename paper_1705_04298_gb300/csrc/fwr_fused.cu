@@ -4,6 +4,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+#include <vector>
+
 #include "fwr_internal.h"
 
 namespace fwr {
@@ -153,6 +156,58 @@ cudaError_t launch_fft2_n(const float2* in, float2* out, int F, int inverse, con
     return cudaGetLastError();
 }
 
+// Per (device, kernel, shared-memory size): the SM count and the resident CTAs
+// per SM (these queries were on every call's path). The kernel's
+// shared-memory limit is a property of the function, so it is tracked per
+// (device, kernel) and only ever raised: a smaller launch never lowers it
+// below what a cached larger launch needs.
+struct KernelLimit {
+    int dev;
+    const void* kern;
+    size_t smem_max;
+};
+struct LaunchShape {
+    int dev;
+    const void* kern;
+    size_t smem;
+    int sms, per_sm;
+};
+
+cudaError_t launch_shape(const void* kern, size_t smem, int threads, int* sms, int* per_sm) {
+    static std::mutex mu;
+    static std::vector<KernelLimit> limits;
+    static std::vector<LaunchShape> cache;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    KernelLimit* lim = nullptr;
+    for (KernelLimit& l : limits)
+        if (l.dev == dev && l.kern == kern) lim = &l;
+    if (!lim || lim->smem_max < smem) {
+        if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem))) != cudaSuccess)
+            return e;
+        if (lim) {
+            lim->smem_max = smem;
+        } else {
+            limits.push_back(KernelLimit{dev, kern, smem});
+        }
+    }
+    for (const LaunchShape& c : cache)
+        if (c.dev == dev && c.kern == kern && c.smem == smem) {
+            *sms = c.sms;
+            *per_sm = c.per_sm;
+            return cudaSuccess;
+        }
+    LaunchShape c{dev, kern, smem, 0, 0};
+    if ((e = cudaDeviceGetAttribute(&c.sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.per_sm, kern, threads, smem)) != cudaSuccess) return e;
+    cache.push_back(c);
+    *sms = c.sms;
+    *per_sm = c.per_sm;
+    return cudaSuccess;
+}
+
 template <typename T, int N>
 cudaError_t launch_n(const Params<T>& p0, cudaStream_t s) {
     // keep the final-filter table in shared memory when it still fits
@@ -160,12 +215,9 @@ cudaError_t launch_n(const Params<T>& p0, cudaStream_t s) {
     p.wf_smem = p.shape != 2 && Layout<T, N>::bytes_wf(p.n) <= size_t(227) * 1024 ? 1 : 0;
     const size_t smem = p.wf_smem ? Layout<T, N>::bytes_wf(p.n) : Layout<T, N>::bytes(p.n);
     auto kern = p.hud ? fused_kernel<T, N, true> : fused_kernel<T, N, false>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    int sms = 0, per_sm = 0;
+    cudaError_t e = launch_shape(reinterpret_cast<const void*>(kern), smem, 4 * N, &sms, &per_sm);
     if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0, per_sm = 0;
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 4 * N, smem)) != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     int grid = sms * per_sm;
     if (p.ctas > 0 && p.ctas < grid) grid = p.ctas;

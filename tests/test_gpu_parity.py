@@ -537,3 +537,24 @@ def test_window_grid_options_and_limits(fwr):
     ref = fwr.Plan(mask, 3.2, fwr.LSQ)
     s = torch.tensor(synth.batch(40, 2, 5, 0.05)[0], dtype=torch.float32, device="cuda")
     assert torch.equal(p128.reconstruct(s, 2), ref.reconstruct(s, 2))
+
+
+def test_alternating_plans_of_one_kernel(fwr):
+    """Plans of one grid whose shared-memory needs differ (the staged pupil
+    grows with n) share the fused kernel; the launcher caches its occupancy
+    per size and only ever raises the kernel's shared-memory limit, so calls
+    alternating between them all launch and repeat bitwise."""
+    plans, inputs, first = [], [], []
+    for n in (64, 40, 24):
+        sl, _, mask = synth.batch(n, 4, 1200 + n, 0.05)
+        pl = fwr.Plan(mask, 128.0 / n if n != 24 else 5.0, fwr.LSQ)
+        assert pl.N == 128
+        plans.append(pl)
+        inputs.append(torch.tensor(sl, dtype=torch.float32, device="cuda"))
+    for pl, s in zip(plans, inputs):
+        first.append(pl.reconstruct(s, 2).clone())
+    for _ in range(2):
+        for pl, s, ref in zip(plans[::-1], inputs[::-1], first[::-1]):
+            assert torch.equal(pl.reconstruct(s, 2), ref)
+    for pl in plans:
+        assert pl.status() == "FWR_OK"
