@@ -15,7 +15,7 @@ import pytest
 
 import oracle
 from paper_1705_04298_gb300 import synth
-from parity_check import errors, max_tol_for, within
+from parity_check import FP32_MAX_256_K10, FP32_MAX_512_K10, errors, max_tol_for, within
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -287,6 +287,39 @@ def test_256_grid(fwr, n, pad, k, periodic, filt):
     for f in range(F):
         ref, _ = run_oracle(sl[f], mask, pad, k, FILTERS[filt], sigma ** 2, r0p, L0p, periodic)
         assert within(ph[f], ref, FP32_TOL, where=str(f))
+
+
+@pytest.mark.parametrize("case", ["256^2 frozen flow, 1000 frames", "512^2, 304 frames"])
+def test_full_size_large_grids_sampled(fwr, case):
+    """The benchmarked large-grid launches (k = 10, LSQ, the launch shape the
+    tuner picks): 128x128 lenslets of frozen-flow frames on 256^2, 1000 frames,
+    and 200x200 lenslets on 512^2, two frames per SM; sampled frames against
+    the oracle, every frame finite with zero mean."""
+    k = 10
+    if case.startswith("256"):
+        sl, _, mask = synth.frozen_flow(128, 32, 7, 0.05, r0=0.12, L0=25.0)
+        pad, F, N = 2.0, 1000, 256
+    else:
+        sl, _, mask = synth.batch(200, 16, 7000, 0.05)
+        pad, F, N = 2.56, 2 * torch.cuda.get_device_properties(0).multi_processor_count, 512
+    reps = (F + len(sl) - 1) // len(sl)
+    s = torch.tensor(sl, dtype=torch.float32, device="cuda").repeat(reps, 1, 1, 1)[:F].contiguous()
+    plan = make_plan(fwr, mask, pad, fwr.LSQ)
+    assert plan.N == N
+    out = torch.empty((F, N, N), device="cuda")
+    plan.autotune(s, k, out)
+    ph = plan.reconstruct(s, k, out)
+    torch.cuda.synchronize()
+    assert plan.status() == "FWR_OK"
+    assert torch.isfinite(ph).all()
+    means = ph.double().mean(dim=(1, 2)).abs().max().item()
+    assert means < 1e-4 * ph.double().std().item()
+    phn = ph.cpu().numpy()
+    # element-wise bound of these ten-iteration large-grid launches (parity_check)
+    max_tol = FP32_MAX_256_K10 if N == 256 else FP32_MAX_512_K10
+    for f in [0, 1, F // 2, F - 2, F - 1]:
+        ref, _ = run_oracle(sl[f % len(sl)], mask, pad, k, oracle.FILTER_LSQ, 0.0, 1.0, 100.0, 0)
+        assert within(phn[f], ref, FP32_TOL, max_tol, where="%s frame %d" % (case, f))
 
 
 def test_256_grid_persistent_tail_and_limits(fwr):
