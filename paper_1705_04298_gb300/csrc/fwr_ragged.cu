@@ -23,6 +23,20 @@ template <int GROUPS>
 __global__ void __launch_bounds__(512, 1)
 ragged_kernel(RaggedParams rp) {
     extern __shared__ __align__(16) unsigned char smem[];
+    // the 128^2 frames' LSQ coefficients live in tensor memory, as in the main
+    // kernel (recomputed at each change of plan; one CTA per SM)
+    __shared__ uint32_t s_tmem;
+    if (threadIdx.x < 32) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                         uint32_t(__cvta_generic_to_shared(&s_tmem))),
+                     "r"(FUSED_TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const uint32_t tmem = s_tmem;
     const int b = blockIdx.x;
     const int i0 = rp.cta_off[b], i1 = rp.cta_off[b + 1];
     float2* G = rp.scratch ? rp.scratch + size_t(b) * SN * SN : nullptr;
@@ -39,15 +53,23 @@ ragged_kernel(RaggedParams rp) {
         }
         const RaggedPlan P = rp.plans[pl];
         if (pl != cur) {
-            if (P.N == 128) fused_setup<float, 128>(fc, smem, P.tab, P.mask, P.n, P.off, P.periodic);
+            if (P.N == 128) fused_setup<float, 128, true>(fc, smem, P.tab, P.mask, P.n, P.off, P.periodic, false, tmem);
             else slab_setup<256>(sc, smem, P.tab, P.mask, P.n, P.off, P.periodic);
             cur = pl;
         }
         bool ok;
-        if (P.N == 128) ok = fused_frame<float, 128>(fc, rp.slopes[f], nullptr, nullptr, rp.phase[f], nullptr, rp.iters);
+        if (P.N == 128)
+            ok = fused_frame<float, 128, true>(fc, rp.slopes[f], nullptr, nullptr, rp.phase[f], nullptr, rp.iters);
         else ok = slab_frame<256, GROUPS>(sc, P.tab, rp.slopes[f], nullptr, rp.phase[f], rp.iters, G);
         if (!ok) atomicOr(P.status, STATUS_NONFINITE);
         __syncthreads();
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(FUSED_TMEM_COLS)
+                     : "memory");
     }
 }
 
