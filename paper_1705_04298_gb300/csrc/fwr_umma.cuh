@@ -221,10 +221,12 @@ __device__ __forceinline__ void epilogue_segment(uint32_t tw, uint4* tile, OutT*
 }
 
 // Destination of the split epilogue: instead of D[M][ldd] (FP32), each output
-// (row i, column (f, x) with f = column / n, x = column mod n) goes to the
-// next product's B operand as BF16 terms: row f n + (i mod n) of B [.][k],
-// column x + n (i >= n), in the term regions of split_b: 3 terms: [hi | lo |
-// hi] at 0, 2n, 4n; 6 terms: [h | m | h | l | m | h] at 0, 2n, .., 10n.
+// (row i < M = 2n, column (f, x) with f = column / n, x = column mod n) goes
+// to the next product's B operand as BF16 terms: row f n + (i mod n) of
+// B [.][k], column x + n (i >= n), in each term region of the row (regions of
+// 2n entries): 3 terms [hi | lo | hi], 6 terms [h | m | h | l | m | h]. With
+// n a multiple of 64, M = 2n is a whole number of 128-row tiles, so every
+// accumulator row of a tile is an output row.
 struct SplitDst {
     __nv_bfloat16* B = nullptr;
     int n = 0, k = 0, terms = 0;
