@@ -68,9 +68,9 @@ bool make_map(CUtensorMap* map, const void* ptr, uint64_t cols, uint64_t rows, u
                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int BN, typename OutT, bool SPLIT = false>
+template <int BN, typename OutT, bool SPLIT = false, bool ARES = false>
 cudaError_t set_smem() {
-    return cudaFuncSetAttribute(fwr::umma::gemm_kernel<BN, GEMM_BK, OutT, SPLIT>,
+    return cudaFuncSetAttribute(fwr::umma::gemm_kernel<BN, GEMM_BK, OutT, SPLIT, ARES>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, int(fwr::umma::Cfg<BN, GEMM_BK>::SMEM));
 }
 
@@ -85,6 +85,9 @@ int device_sms(int device) {
     if (set_smem<128, float>() != cudaSuccess || set_smem<256, float>() != cudaSuccess ||
         set_smem<128, __nv_bfloat16>() != cudaSuccess || set_smem<256, __nv_bfloat16>() != cudaSuccess ||
         set_smem<128, float, true>() != cudaSuccess || set_smem<256, float, true>() != cudaSuccess ||
+        set_smem<128, float, false, true>() != cudaSuccess || set_smem<256, float, false, true>() != cudaSuccess ||
+        set_smem<128, __nv_bfloat16, false, true>() != cudaSuccess ||
+        set_smem<256, __nv_bfloat16, false, true>() != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || sms < 1)
         return 0;
     done.push_back({device, sms});
@@ -119,18 +122,33 @@ cudaError_t launch_gemm(const CUtensorMap& ma, const CUtensorMap& mb128, const C
     cfg.numAttrs = pdl ? 1 : 0;
     const int n32 = int(N);
     const bool split = sd.B != nullptr;
+    // A resident in shared memory when every tile of a CTA has the same A rows
+    // (tiles walk M fastest, so a grid that is a multiple of the M tiles keeps
+    // each CTA on one row block) and K fits its k-blocks
+    const int kblocks = (K + GEMM_BK - 1) / GEMM_BK;
+    const bool ares = !split && kblocks <= fwr::umma::Cfg<128, GEMM_BK>::ARES_KB &&
+                      (grid % unsigned(tm) == 0 || tiles <= (long long)grid);
+    using namespace fwr::umma;
     if (bn == 256) {
-        cfg.dynamicSmemBytes = fwr::umma::Cfg<256, GEMM_BK>::SMEM;
-        return split ? cudaLaunchKernelEx(&cfg, fwr::umma::gemm_kernel<256, GEMM_BK, OutT, true>, ma, mb256, M, n32,
-                                          K, D, ldd, status, wait_limit, sd)
-                     : cudaLaunchKernelEx(&cfg, fwr::umma::gemm_kernel<256, GEMM_BK, OutT, false>, ma, mb256, M, n32,
-                                          K, D, ldd, status, wait_limit, sd);
+        cfg.dynamicSmemBytes = Cfg<256, GEMM_BK>::SMEM;
+        if (split)
+            return cudaLaunchKernelEx(&cfg, gemm_kernel<256, GEMM_BK, OutT, true>, ma, mb256, M, n32, K, D, ldd,
+                                      status, wait_limit, sd);
+        if (ares)
+            return cudaLaunchKernelEx(&cfg, gemm_kernel<256, GEMM_BK, OutT, false, true>, ma, mb256, M, n32, K, D,
+                                      ldd, status, wait_limit, sd);
+        return cudaLaunchKernelEx(&cfg, gemm_kernel<256, GEMM_BK, OutT, false>, ma, mb256, M, n32, K, D, ldd, status,
+                                  wait_limit, sd);
     }
-    cfg.dynamicSmemBytes = fwr::umma::Cfg<128, GEMM_BK>::SMEM;
-    return split ? cudaLaunchKernelEx(&cfg, fwr::umma::gemm_kernel<128, GEMM_BK, OutT, true>, ma, mb128, M, n32, K,
-                                      D, ldd, status, wait_limit, sd)
-                 : cudaLaunchKernelEx(&cfg, fwr::umma::gemm_kernel<128, GEMM_BK, OutT, false>, ma, mb128, M, n32, K,
-                                      D, ldd, status, wait_limit, sd);
+    cfg.dynamicSmemBytes = Cfg<128, GEMM_BK>::SMEM;
+    if (split)
+        return cudaLaunchKernelEx(&cfg, gemm_kernel<128, GEMM_BK, OutT, true>, ma, mb128, M, n32, K, D, ldd, status,
+                                  wait_limit, sd);
+    if (ares)
+        return cudaLaunchKernelEx(&cfg, gemm_kernel<128, GEMM_BK, OutT, false, true>, ma, mb128, M, n32, K, D, ldd,
+                                  status, wait_limit, sd);
+    return cudaLaunchKernelEx(&cfg, gemm_kernel<128, GEMM_BK, OutT, false>, ma, mb128, M, n32, K, D, ldd, status,
+                              wait_limit, sd);
 }
 
 }  // namespace

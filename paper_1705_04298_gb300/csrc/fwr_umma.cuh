@@ -22,6 +22,8 @@
 //                    instruction writes four whole 128-byte rows, then an
 //                    arrive on the accumulator's "empty" barrier, so the next
 //                    tile's MMAs run meanwhile
+// With every tile of a CTA on the same A rows and K within four k-blocks, A
+// is loaded once per CTA and the stages carry B only (ARES).
 // Every mbarrier wait gives up after about two seconds (clock64), sets the
 // CTA's abort flag and the caller's status word; the roles then skip their
 // work, the producer waits (bounded) for its loads in flight, the issuer for
@@ -71,6 +73,11 @@ struct Cfg {
     static constexpr uint32_t EPI_BYTES = 4 * 32 * 128;
     // stages + epilogue staging + 1 KB alignment slack + barriers and flags
     static constexpr size_t SMEM = size_t(STAGES) * STAGE_BYTES + EPI_BYTES + 1024 + 512;
+    // resident-A variant (K <= ARES_KB * BK): the CTA's A rows loaded once,
+    // the same 192 KB holding them and a ring of B-only stages
+    static constexpr int ARES_KB = 4;
+    static constexpr int ARES_STAGES = int((uint32_t(STAGES) * STAGE_BYTES - ARES_KB * A_BYTES) / B_BYTES);
+    static_assert(ARES_KB * A_BYTES + ARES_STAGES * B_BYTES <= uint32_t(STAGES) * STAGE_BYTES, "resident A fits");
 };
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return uint32_t(__cvta_generic_to_shared(p)); }
@@ -316,24 +323,30 @@ __device__ __forceinline__ void mbar_drain(uint32_t bar, uint32_t parity, volati
 // producer's waits and every drain of work in flight keep WAIT_LIMIT.
 // SPLIT: the epilogue writes split BF16 terms to sd instead of D (a separate
 // instantiation, so the plain products keep their register budget).
-template <int BN, int BK, typename OutT, bool SPLIT = false>
+// ARES: every tile of the CTA has the same A rows (the launcher guarantees it:
+// the grid is a multiple of the M tiles, or one tile per CTA) and K fits
+// Cfg::ARES_KB k-blocks: A is loaded once per CTA and the stages carry B only.
+template <int BN, int BK, typename OutT, bool SPLIT = false, bool ARES = false>
 __global__ void __launch_bounds__(THREADS, 1)
     gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int M, int N,
                 int K, OutT* __restrict__ D, long long ldd, int* status, long long wait_limit, SplitDst sd) {
     typedef Cfg<BN, BK> C;
-    constexpr int S = C::STAGES;
+    constexpr int S = ARES ? C::ARES_STAGES : C::STAGES;
+    constexpr uint32_t SB = ARES ? C::B_BYTES : C::STAGE_BYTES;       // bytes per stage
+    constexpr uint32_t RES = ARES ? C::ARES_KB * C::A_BYTES : 0u;     // resident A ahead of the stages
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = su32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
     uint8_t* const gbase = smem_raw + (base - raw);
-    // barriers: full[S], empty[S], acc_full[2], acc_empty[2], mma_done; then
-    // the TMEM address and the abort flag
-    uint4* const epi = reinterpret_cast<uint4*>(gbase + S * C::STAGE_BYTES);
-    uint64_t* const bars = reinterpret_cast<uint64_t*>(gbase + S * C::STAGE_BYTES + C::EPI_BYTES);
-    uint32_t* const tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * S + 5);
+    const uint32_t sbase = base + RES;
+    // barriers: full[S], empty[S], acc_full[2], acc_empty[2], mma_done,
+    // a_full; then the TMEM address and the abort flag
+    uint4* const epi = reinterpret_cast<uint4*>(gbase + C::STAGES * C::STAGE_BYTES);
+    uint64_t* const bars = reinterpret_cast<uint64_t*>(gbase + C::STAGES * C::STAGE_BYTES + C::EPI_BYTES);
+    uint32_t* const tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * S + 6);
     volatile int* const abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
     const uint32_t full0 = su32(bars), empty0 = full0 + 8 * S, accf0 = empty0 + 8 * S, acce0 = accf0 + 16,
-                   mma_done = acce0 + 16;
+                   mma_done = acce0 + 16, a_full = mma_done + 8;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tiles_m = (M + BM - 1) / BM, tiles = tiles_m * (N / BN), kblocks = (K + BK - 1) / BK;
 
@@ -347,6 +360,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             mbar_init(acce0 + 8 * b, 4);  // one arrive per epilogue warp
         }
         mbar_init(mma_done, 1);
+        mbar_init(a_full, 1);
         *abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
         asm volatile("prefetch.tensormap [%0];\n" ::"l"(reinterpret_cast<uint64_t>(&mapA)) : "memory");
@@ -373,6 +387,13 @@ __global__ void __launch_bounds__(THREADS, 1)
             // producer
             int it = 0;
             bool ok = true;
+            if constexpr (ARES) {
+                if (blockIdx.x < tiles) {
+                    const int m0 = (blockIdx.x % tiles_m) * BM;
+                    mbar_expect_tx(a_full, uint32_t(kblocks) * C::A_BYTES);
+                    for (int kb = 0; kb < kblocks; ++kb) tma_load_2d(base + kb * C::A_BYTES, &mapA, kb * BK, m0, a_full);
+                }
+            }
             for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
                 const int m0 = (t % tiles_m) * BM, n0 = (t / tiles_m) * BN;
                 for (int kb = 0; kb < kblocks; ++kb, ++it) {
@@ -381,14 +402,21 @@ __global__ void __launch_bounds__(THREADS, 1)
                         ok = false;
                         break;
                     }
-                    const uint32_t sa = base + s * C::STAGE_BYTES, sb = sa + C::A_BYTES;
-                    mbar_expect_tx(full0 + 8 * s, C::STAGE_BYTES);
-                    tma_load_2d(sa, &mapA, kb * BK, m0, full0 + 8 * s);
-                    tma_load_2d(sb, &mapB, kb * BK, n0, full0 + 8 * s);
+                    if constexpr (ARES) {
+                        const uint32_t sb = sbase + s * SB;
+                        mbar_expect_tx(full0 + 8 * s, C::B_BYTES);
+                        tma_load_2d(sb, &mapB, kb * BK, n0, full0 + 8 * s);
+                    } else {
+                        const uint32_t sa = sbase + s * SB, sb = sa + C::A_BYTES;
+                        mbar_expect_tx(full0 + 8 * s, C::STAGE_BYTES);
+                        tma_load_2d(sa, &mapA, kb * BK, m0, full0 + 8 * s);
+                        tma_load_2d(sb, &mapB, kb * BK, n0, full0 + 8 * s);
+                    }
                 }
             }
             // every load issued must land before the CTA may exit
             for (int j = it > S ? it - S : 0; j < it; ++j) mbar_drain(full0 + 8 * (j % S), uint32_t(j / S) & 1u, abort);
+            if (ARES && blockIdx.x < tiles) mbar_drain(a_full, 0u, abort);
         }
         __syncwarp();
     } else if (warp == 1) {
@@ -401,6 +429,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                 if (ub > 0 && !mbar_wait(acce0 + 8 * b, uint32_t(ub - 1) & 1u, abort, wait_limit)) break;
                 fence_after();
                 const uint32_t d = tmem + uint32_t(b * BN);
+                if (ARES && jt == 0 && !mbar_wait(a_full, 0u, abort, wait_limit)) break;
                 for (int kb = 0; kb < kblocks; ++kb, ++it) {
                     const int s = it % S, use = it / S;
                     if (!mbar_wait(full0 + 8 * s, uint32_t(use) & 1u, abort, wait_limit)) {
@@ -408,7 +437,8 @@ __global__ void __launch_bounds__(THREADS, 1)
                         break;
                     }
                     fence_after();
-                    const uint32_t sa = base + s * C::STAGE_BYTES, sb = sa + C::A_BYTES;
+                    const uint32_t sa = ARES ? base + kb * C::A_BYTES : sbase + s * SB;
+                    const uint32_t sb = ARES ? sbase + s * SB : sa + C::A_BYTES;
 #pragma unroll
                     for (int k = 0; k < BK / 16; ++k)
                         mma_bf16(d, sdesc(sa + 32u * k, C::SBO, C::SWIZZLE), sdesc(sb + 32u * k, C::SBO, C::SWIZZLE),

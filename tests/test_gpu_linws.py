@@ -29,11 +29,16 @@ def bf16(x):
 
 
 @pytest.mark.parametrize("M,N,K", [(1, 128, 8), (100, 128, 64), (128, 256, 72), (300, 384, 1000),
-                                   (257, 128, 2560), (1000, 1280, 2528), (600, 8192, 128), (1000, 32768, 64)])
+                                   (257, 128, 2560), (1000, 1280, 2528), (600, 8192, 128), (1000, 32768, 64),
+                                   (1000, 32768, 256), (256, 8192, 200)])
 def test_gemm_matches_fp64_reference(fwr, M, N, K):
     """Rows beyond M and K beyond a multiple of 64 come from the TMA zero fill;
-    N = 384 and 128 take 128-wide tiles, the rest 256-wide; the last two
-    shapes give some CTAs several tiles (both TMEM accumulators in turn)."""
+    N = 384 and 128 take 128-wide tiles, the rest 256-wide; (600, 8192, 128)
+    and the 32768-wide shapes give some CTAs several tiles (both TMEM
+    accumulators in turn). K <= 256 with a grid that is a multiple of the M
+    tiles (or one tile per CTA) keeps A resident in shared memory: the small
+    shapes, (1000, 32768, 64 / 256) over several tiles per CTA and
+    (256, 8192, 200) with a partial last k-block."""
     g = torch.Generator().manual_seed(M * 7 + N + K)
     A = torch.randn(M, K, generator=g).bfloat16()
     B = torch.randn(N, K, generator=g).bfloat16()
